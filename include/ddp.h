@@ -1,0 +1,242 @@
+/*
+ * ddp.h - C ABI of libddp: domain-restricted Wilson-Dirac quark propagators
+ * and their Wick contractions on one NVIDIA GB300 (sm_103a).
+ *
+ * The library computes the propagators S^(i) = D_{Gamma_i}^{-1} of the
+ * Wilson-Dirac operator restricted to a box-shaped domain Gamma_i with
+ * Dirichlet faces (Sec. 2, Eq. blkdec and Eq. diric of Ce, Giusti, Schaefer,
+ * "Domain decomposition, multi-level integration and exponential noise
+ * reduction in lattice QCD"), the terms of the telescoping series
+ * S = S^(0) + sum_i [S^(i) - S^(i-1)] (Sec. 1, Eq. Dseries) and the Wick
+ * contractions that consume them (Sec. 3 Eq. W0, Sec. 4 Eq. W0pc and the
+ * nucleon two-point function, Sec. 5 Eq. factsing).
+ *
+ * Operator (App. A): D = D_w + m0, 2 kappa D = 1 - kappa D_hop (Sec. 5), i.e.
+ *   (D psi)(y) = psi(y)/(2 kappa)
+ *              - 1/2 sum_mu [ (1 - g_mu) U_mu(y) psi(y+mu) + (1 + g_mu) U_mu(y-mu)^+ psi(y-mu) ].
+ * D_Gamma drops every term that involves a site outside the domain.
+ *
+ * Conventions shared by every call
+ *  - Lattice L0 x L1 x L2 x L3, direction 0 is time, every L_mu even and >= 2.
+ *    Global site index ((x0*L1 + x1)*L2 + x2)*L3 + x3.
+ *  - Complex numbers are interleaved (re, im) doubles.
+ *  - Gauge field U[mu][site][row][col] (4*V*9 complex).  Links must be SU(3)
+ *    (unitary, det 1, to 1e-8): the low-precision copies keep two rows and
+ *    rebuild the third.
+ *  - A domain is a box {(o_mu + k_mu) mod L_mu : 0 <= k_mu < e_mu}.  If
+ *    e_mu == L_mu the direction is not restricted and the global boundary
+ *    condition holds; otherwise both faces are Dirichlet.  Boxes may wrap
+ *    around the lattice.  e_3 must be even.  Domain-local site order is
+ *    lexicographic in k with the nesting of the global index.
+ *  - Spinor fields are [ncol][n_sites][spin 4][colour 3] complex in
+ *    domain-local order.  The 12 columns of a point-source propagator are
+ *    ordered c = 3*spin + colour: S(y,x)_{alpha a, beta b} = S_out[3 beta + b][y][alpha][a].
+ *  - Gamma matrices (Euclidean, chiral basis): g_0 = [[0,1],[1,0]],
+ *    g_k = [[0,-i s_k],[i s_k,0]], g_5 = g_0 g_1 g_2 g_3.
+ *  - Ownership: the caller owns every input and output buffer.  Buffers may
+ *    be device memory or host memory (detected per pointer); the library never
+ *    frees or retains them after a call returns.  ddp_load_gauge copies.
+ *  - Calls are ordered on the context's CUDA stream.  Calls that return a
+ *    status that depends on device results (solves, contractions to host
+ *    memory) synchronise that stream before returning.
+ *  - Every call returns a ddp_status.  On error, outputs are unspecified
+ *    unless stated otherwise, and the context stays usable.
+ */
+#ifndef DDP_H
+#define DDP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DDP_OK = 0,
+    DDP_ERR_INVALID_ARG = 1,   /* bad size, box, source, kappa, id or non-SU(3)/non-finite links */
+    DDP_ERR_UNSUPPORTED = 2,   /* csw != 0, odd lattice extent, odd e_3 */
+    DDP_ERR_OOM = 3,           /* device allocation failed or over the context's memory budget */
+    DDP_ERR_NOT_CONVERGED = 4, /* a solve missed its tolerance within the iteration caps */
+    DDP_ERR_CUDA = 5,          /* a CUDA runtime error (message in ddp_last_error) */
+    DDP_ERR_BUSY = 6,          /* serving: no slot or memory free now, retry later */
+    DDP_ERR_NOT_FOUND = 7      /* unknown gauge, domain or ticket id */
+} ddp_status;
+
+typedef enum { DDP_BC_PERIODIC = 0, DDP_BC_ANTIPERIODIC = 1, DDP_BC_OPEN = 2 } ddp_time_bc;
+
+/* Arithmetic of a solve.  FP64: every vector and link in FP64 (the plain
+ * path).  MIXED_*: inner Krylov iterations in FP32 arithmetic on FP32 / FP16
+ * (per-site scaled spinors) / BF16 storage of spinors and 2-row links; the
+ * true residual, the accumulation of the solution and the norms that decide
+ * convergence are FP64 (defect correction). */
+typedef enum {
+    DDP_PREC_FP64 = 0,
+    DDP_PREC_MIXED_FP32 = 1,
+    DDP_PREC_MIXED_FP16 = 2,
+    DDP_PREC_MIXED_BF16 = 3
+} ddp_precision;
+
+typedef enum {
+    DDP_CONTRACT_PSEUDO_LOCAL = 0, /* tr{g5 S(x,x)} at the point source (Eq. W0), C_out[0] */
+    DDP_CONTRACT_PSEUDO_NOISE = 1, /* sum_{x vec} sum_c eta_c^+ g5 psi_c per time slice (Sec. 5) */
+    DDP_CONTRACT_NUCLEON = 2,      /* sum_{y vec} [W_N1 - W_N2](y,x) per time slice (Sec. 4) */
+    DDP_CONTRACT_PION = 3          /* sum_{y vec} tr{S S^+}(y,x) per time slice (Eq. W0pc) */
+} ddp_contract_kind;
+
+#define DDP_INFO_COLS 12
+
+typedef struct {
+    int status;             /* DDP_OK or DDP_ERR_NOT_CONVERGED */
+    int ncol;
+    int outer_cycles;       /* FP64 true-residual recomputations */
+    int inner_iters;        /* BiCGStab iterations summed over outer cycles (max over columns) */
+    double max_rel_residual;                    /* max over columns of |eta - D_Gamma psi| / |eta| (FP64) */
+    double rel_residual[DDP_INFO_COLS];         /* per column, first DDP_INFO_COLS columns */
+    double seconds;         /* wall time of the call */
+} ddp_solve_info;
+
+typedef struct ddp_ctx ddp_ctx;
+
+/* Text of a status code (static storage). */
+const char *ddp_error_string(int status);
+/* Text of the last CUDA error seen by this context (static per context). */
+const char *ddp_last_error(const ddp_ctx *ctx);
+int ddp_version(void);
+
+/* Create a context on CUDA device `device`, ordered on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The context owns all
+ * internal device memory. */
+int ddp_create(ddp_ctx **ctx, int device, void *cuda_stream);
+int ddp_destroy(ddp_ctx *ctx);
+int ddp_set_stream(ddp_ctx *ctx, void *cuda_stream);
+
+/* Gauge field U_mu(x), the link variables of App. A.  Copies U (host or
+ * device, [4][V][3][3] complex) into a resident FP64 copy plus 2-row FP32,
+ * FP16 and BF16 copies in an even-odd site order.  time_bc: ddp_time_bc.
+ * Rejects non-finite or non-SU(3) links with DDP_ERR_INVALID_ARG. */
+int ddp_load_gauge(ddp_ctx *ctx, const double *U, const int L[4], int time_bc, int *gauge_id);
+
+/* A level-1 variant (Sec. 3 two-level integration): a new gauge field equal
+ * to base_gauge_id except for the links U_mu(x) with x in the box, which are
+ * replaced by U_box[4][n_box][3][3] (box-local order).  Used to re-solve
+ * domain propagators for updates of the links inside one region. */
+int ddp_load_gauge_region(ddp_ctx *ctx, int base_gauge_id, const int origin[4], const int extent[4],
+                          const double *U_box, int *gauge_id);
+int ddp_free_gauge(ddp_ctx *ctx, int gauge_id);
+
+/* Domain Gamma (Sec. 2): a box on a loaded gauge field. */
+int ddp_set_domain(ddp_ctx *ctx, int gauge_id, const int origin[4], const int extent[4], int *domain_id);
+int ddp_free_domain(ddp_ctx *ctx, int domain_id);
+
+/* Index maps of a domain, computed on the device: for each domain-local
+ * site, its global site index and its even-odd index (rank among the
+ * domain's sites of the same global parity, in domain-local order).  Output
+ * pointers may be NULL. */
+int ddp_domain_sites(ddp_ctx *ctx, int domain_id, int64_t *n_sites, int64_t *global_index_out,
+                     int64_t *eo_index_out);
+
+/* out = D_Gamma psi for ncol columns (App. A, Sec. 2).  precision FP64 uses
+ * the FP64 links; the MIXED_* values apply the low-precision stencil of the
+ * inner solver (FP32 arithmetic on the stored copies). */
+int ddp_apply_dirac(ddp_ctx *ctx, int domain_id, double kappa, const double *psi, double *out, int ncol,
+                    int precision);
+
+/* Domain propagator S^(i)(y,x) = D_Gamma^{-1}(y,x) (Eq. diric) for the 12
+ * spin-colour point sources at global site src (which must lie in the
+ * domain).  Stops when every column has |eta - D_Gamma psi|_2 / |eta|_2 <= tol
+ * (FP64, unpreconditioned operator).  csw must be 0 (no clover term).
+ * S_out: [12][n_sites][4][3].  On DDP_ERR_NOT_CONVERGED S_out holds the best
+ * iterate and info the residuals.  info may be NULL. */
+int ddp_solve_propagator(ddp_ctx *ctx, int domain_id, double kappa, double csw, const int src[4], double tol,
+                         int precision, double *S_out, ddp_solve_info *info);
+
+/* psi_c = D_Gamma^{-1} eta_c for ncol arbitrary sources eta [ncol][n][4][3]. */
+int ddp_solve_sources(ddp_ctx *ctx, int domain_id, double kappa, double csw, const double *eta, int ncol,
+                      double tol, int precision, double *psi_out, ddp_solve_info *info);
+
+/* One request of a batched solve. */
+typedef struct {
+    int domain_id;
+    double kappa;
+    double csw;          /* must be 0 */
+    int src[4];          /* point source (used when eta == NULL) */
+    const double *eta;   /* NULL: 12 point-source columns at src; else ncol sources */
+    int ncol;            /* 12 for point sources */
+    double tol;
+    double *out;         /* [ncol][n_sites][4][3] */
+} ddp_solve_req;
+
+/* Many independent domain solves (different domains, gauge fields, kappas)
+ * in one device-driven launch sequence: all columns of all requests iterate
+ * together inside a graph-captured loop.  All requests use `precision`.
+ * infos: n entries or NULL.  Returns DDP_ERR_NOT_CONVERGED if any request
+ * missed its tolerance (its info says which). */
+int ddp_solve_batch(ddp_ctx *ctx, const ddp_solve_req *reqs, int n, int precision, ddp_solve_info *infos);
+
+/* Series term T^(i) = S^(i) - E S^(i-1) on the big domain (Eq. Dseries), where
+ * E extends S_small by zero outside the small domain; the small domain must
+ * lie inside the big one.  S_small [ncol][n_small][4][3], S_big and T_out
+ * [ncol][n_big][4][3]. */
+int ddp_series_terms(ddp_ctx *ctx, int domain_small, const double *S_small, int domain_big, const double *S_big,
+                     double *T_out, int ncol);
+
+/* Wick contractions of a solved propagator on a domain.
+ *  PSEUDO_LOCAL: S = 12 point-source columns, src = the source; C_out[2] = tr{g5 S(x,x)}.
+ *  PSEUDO_NOISE: S = psi_c = D_Gamma^{-1} eta_c, eta = the ncol sources;
+ *                C_out[2*L0] = sum_{x vec} sum_c eta_c^+ g5 psi_c by global time slice.
+ *  NUCLEON:      S = 12 point-source columns, u = d = S, C = i g0 g2, P- = (1 - g0)/2;
+ *                C_out[2*L0] = sum_{y vec} [W_N1 - W_N2](y, x).
+ *  PION:         C_out[2*L0] = sum_{y vec} tr{S(y,x) S(y,x)^+} (imaginary parts 0).
+ * Time slices outside the domain are 0.  C_out is host or device memory. */
+int ddp_contract(ddp_ctx *ctx, int kind, int domain_id, const double *S, const double *eta, int ncol,
+                 const int src[4], double *C_out);
+
+/* ---- serving: continuous batching of propagator solves ------------------
+ * Requests are admitted while the context's memory budget and slot count
+ * allow; admitted requests join the running device loop at its next
+ * admission point, so work of requests that arrive while others run
+ * overlaps on the GPU.  Each result equals the result of the same request
+ * solved alone (deterministic per-request reductions). */
+
+/* Configure serving: memory budget in bytes for solver state (0 = 80% of
+ * free device memory) and the maximum number of concurrently active requests. */
+int ddp_serve_config(ddp_ctx *ctx, uint64_t mem_budget_bytes, int max_active, int precision);
+/* Submit a request; DDP_ERR_BUSY if it does not fit now.  ticket receives an id. */
+int ddp_submit(ddp_ctx *ctx, const ddp_solve_req *req, uint64_t *ticket);
+/* Advance the serving loop by one step (admit, iterate, retire). Non-blocking
+ * beyond the step itself; returns the number of requests still in flight in *in_flight. */
+int ddp_serve_step(ddp_ctx *ctx, int *in_flight);
+/* done = 1 when the request finished (its out buffer is then complete). */
+int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
+
+/* ---- tuning and measurement ---------------------------------------------- */
+
+/* Solver knobs: "max_outer" (defect-correction cycles), "max_inner"
+ * (BiCGStab iterations per cycle), "delta_fp64" / "delta_fp32" /
+ * "delta_fp16" / "delta_bf16" (smallest inner relative tolerance per storage
+ * format), "tile_sites" (sites per block, multiple of 32, 0 = automatic),
+ * "tile_cols" (columns per block, 0 = automatic), "conditional" (1: the
+ * inner loop is a device-driven CUDA-graph WHILE node; 0: host-polled graph
+ * chunks).  DDP_ERR_INVALID_ARG for unknown names or values. */
+int ddp_set_param(ddp_ctx *ctx, const char *name, double value);
+
+/* Average duration (ms) of the inner-loop stencil kernel (Schur-complement
+ * hop with fused epilogue and dot product) on a domain with ncol columns in
+ * the given storage format, timed with CUDA events over `iters` launches on
+ * the context's stream; bytes_per_launch receives the kernel's algorithmic
+ * HBM bytes (input, operand, shadow residual and output half-spinors plus
+ * the links touching the output sites). */
+int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters,
+                 float *ms_per_launch, double *bytes_per_launch);
+
+/* Number of kernels this context has launched so far. */
+long ddp_kernel_launches(const ddp_ctx *ctx);
+
+/* Clears the serving state (pending and finished requests). */
+int ddp_serve_reset(ddp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDP_H */

@@ -1,0 +1,370 @@
+// Wick contractions of domain propagators (FP64):
+//   - local disconnected trace tr{g5 S(x,x)} (Sec. 3, Eq. W0),
+//   - stochastic time-slice trace sum_{x vec} sum_c eta_c^+ g5 psi_c (Sec. 5),
+//   - pion sum_{y vec} tr{S S^+} (Sec. 4, Eq. W0pc with the exact S),
+//   - nucleon sum_{y vec} [W_N1 - W_N2](y,x) (Sec. 4).
+// Per time slice: blocks reduce a chunk of the slice to a partial (warp
+// shuffles, fixed order), a second kernel adds a slice's partials in order.
+#include <cstring>
+
+#include "ddp_host.h"
+
+namespace ddp {
+
+// Chiral basis: g5 = diag(-1,-1,1,1); C g5 = diag(s2, s2) with s2 = [[0,-i],[i,0]];
+// P- = (1 - g0)/2 with g0 = [[0,1],[1,0]] (2x2 blocks).
+
+struct Cplx {
+    double re, im;
+};
+__device__ __forceinline__ Cplx cadd(Cplx a, Cplx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ Cplx csub(Cplx a, Cplx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ Cplx cmulc(Cplx a, Cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ Cplx cscale(double s, Cplx a) { return {s * a.re, s * a.im}; }
+__device__ __forceinline__ Cplx timesi(Cplx a) { return {-a.im, a.re}; }
+__device__ __forceinline__ Cplx timesmi(Cplx a) { return {a.im, -a.re}; }
+
+struct ContractArgs {
+    Item it;
+    const double2 *S;    // [ncol][n][12]
+    const double2 *eta;  // [ncol][n][12] (noise kind)
+    int ncol;
+    int kind;
+    int nchunk;          // blocks per local time slice
+    double2 *part;       // [e0][nchunk]
+};
+
+__device__ __forceinline__ Cplx ld(const double2 *p) {
+    double2 v = __ldg(p);
+    return {v.x, v.y};
+}
+
+// M[rho][sigma] = S(y,x)_{rho a, sigma b} for colours (a, b) from the site's 144 entries in smem.
+__device__ __forceinline__ void spin_block(const Cplx *site, int a, int b, Cplx M[4][4]) {
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int s = 0; s < 4; s++) M[r][s] = site[(3 * s + b) * 12 + 3 * r + a];
+}
+
+// (C g5) M : rows permuted with phases
+__device__ __forceinline__ void cg5_left(const Cplx M[4][4], Cplx O[4][4]) {
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        O[0][s] = timesmi(M[1][s]);
+        O[1][s] = timesi(M[0][s]);
+        O[2][s] = timesmi(M[3][s]);
+        O[3][s] = timesi(M[2][s]);
+    }
+}
+// M (C g5)
+__device__ __forceinline__ void cg5_right(const Cplx M[4][4], Cplx O[4][4]) {
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        O[r][0] = timesi(M[r][1]);
+        O[r][1] = timesmi(M[r][0]);
+        O[r][2] = timesi(M[r][3]);
+        O[r][3] = timesmi(M[r][2]);
+    }
+}
+// M P-  (P- = 1/2 [[1,-1],[-1,1]] in 2x2 blocks)
+__device__ __forceinline__ void pminus_right(const Cplx M[4][4], Cplx O[4][4]) {
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        Cplx d0 = cscale(0.5, csub(M[r][0], M[r][2]));
+        Cplx d1 = cscale(0.5, csub(M[r][1], M[r][3]));
+        O[r][0] = d0;
+        O[r][1] = d1;
+        O[r][2] = {-d0.re, -d0.im};
+        O[r][3] = {-d1.re, -d1.im};
+    }
+}
+
+__constant__ int kPerm[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {2, 1, 0}, {1, 0, 2}};
+__constant__ double kSign[6] = {1, 1, 1, -1, -1, -1};
+
+// W_N1 - W_N2 at one sink site with u = d = S:
+//   W_N1 = eps^{abc} eps^{feg} tr[S^{ag T} C g5 S^{bf} C g5] tr[S^{ce} P-]
+//   W_N2 = eps^{abc} eps^{feg} tr[S^{ag T} C g5 S^{be} P- S^{cf} C g5]
+__device__ Cplx nucleon_site(const Cplx *site) {
+    Cplx w1 = {0, 0}, w2 = {0, 0};
+    for (int p1 = 0; p1 < 6; p1++) {
+        int a = kPerm[p1][0], b = kPerm[p1][1], c = kPerm[p1][2];
+        for (int p2 = 0; p2 < 6; p2++) {
+            int f = kPerm[p2][0], e = kPerm[p2][1], g = kPerm[p2][2];
+            double sg = kSign[p1] * kSign[p2];
+            Cplx Sag[4][4], M[4][4], X[4][4], Y[4][4], Z[4][4];
+            spin_block(site, a, g, Sag);
+            // W_N1: tr[Sag^T (C g5 Sbf C g5)] * tr[Sce P-]
+            spin_block(site, b, f, M);
+            cg5_left(M, X);
+            cg5_right(X, Y);
+            Cplx t1 = {0, 0};
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int s = 0; s < 4; s++) t1 = cadd(t1, cmulc(Sag[r][s], Y[r][s]));
+            spin_block(site, c, e, M);
+            Cplx t2 = cscale(0.5, cadd(csub(M[0][0], M[0][2]), csub(M[1][1], M[1][3])));
+            t2 = cadd(t2, cscale(0.5, cadd(csub(M[2][2], M[2][0]), csub(M[3][3], M[3][1]))));
+            w1 = cadd(w1, cscale(sg, cmulc(t1, t2)));
+            // W_N2: tr[Sag^T (C g5 Sbe P-) (Scf C g5)]
+            spin_block(site, b, e, M);
+            cg5_left(M, X);
+            pminus_right(X, Y);
+            spin_block(site, c, f, M);
+            cg5_right(M, X);
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int s = 0; s < 4; s++) {
+                    Cplx z = {0, 0};
+#pragma unroll
+                    for (int k = 0; k < 4; k++) z = cadd(z, cmulc(Y[r][k], X[k][s]));
+                    Z[r][s] = z;
+                }
+            Cplx t3 = {0, 0};
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int s = 0; s < 4; s++) t3 = cadd(t3, cmulc(Sag[r][s], Z[r][s]));
+            w2 = cadd(w2, cscale(sg, t3));
+        }
+    }
+    return csub(w1, w2);
+}
+
+__device__ __forceinline__ void block_sum_to(double2 *dst, Cplx v) {
+    __shared__ double sre[32], sim[32];
+    double re = warp_sum(v.re), im = warp_sum(v.im);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sre[w] = re;
+        sim[w] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int i = 0; i < (int)(blockDim.x + 31) / 32; i++) {
+            a += sre[i];
+            b += sim[i];
+        }
+        *dst = make_double2(a, b);
+    }
+}
+
+// grid (nchunk, e0); one thread per site of the slice.
+__global__ void k_contract_slice(ContractArgs a) {
+    extern __shared__ Cplx site_smem[];
+    const Item &it = a.it;
+    int slice_n = it.e[1] * it.e[2] * it.e[3];
+    int n = 2 * it.nh;
+    int t = blockIdx.y;
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = r < slice_n;
+    int l = t * slice_n + (ok ? r : 0);
+    Cplx v = {0, 0};
+    if (a.kind == DDP_CONTRACT_NUCLEON) {
+        Cplx *site = site_smem + threadIdx.x * 144;
+        if (ok) {
+            for (int c = 0; c < 12; c++)
+                for (int j = 0; j < 12; j++) site[c * 12 + j] = ld(a.S + ((int64_t)c * n + l) * 12 + j);
+            v = nucleon_site(site);
+        }
+    } else if (ok) {
+        for (int c = 0; c < a.ncol; c++) {
+            const double2 *ps = a.S + ((int64_t)c * n + l) * 12;
+            if (a.kind == DDP_CONTRACT_PION) {
+                for (int j = 0; j < 12; j++) {
+                    Cplx s = ld(ps + j);
+                    v.re += s.re * s.re + s.im * s.im;
+                }
+            } else {  // noise trace: eta^+ g5 psi, g5 = diag(-1,-1,1,1) on spin
+                const double2 *pe = a.eta + ((int64_t)c * n + l) * 12;
+                for (int j = 0; j < 12; j++) {
+                    Cplx e = ld(pe + j), s = ld(ps + j);
+                    double g5 = (j < 6) ? -1.0 : 1.0;
+                    v.re += g5 * (e.re * s.re + e.im * s.im);
+                    v.im += g5 * (e.re * s.im - e.im * s.re);
+                }
+            }
+        }
+    }
+    block_sum_to(a.part + (int64_t)t * a.nchunk + blockIdx.x, v);
+}
+
+// One block per global time slice: fixed-order sum of the slice's partials.
+__global__ void k_contract_final(Item it, const double2 *part, int nchunk, double2 *out) {
+    int y0 = blockIdx.x;
+    int t = y0 - it.o[0];
+    if (t < 0) t += it.L[0];
+    __shared__ double sre[256], sim[256];
+    double re = 0, im = 0;
+    if (t < it.e[0]) {
+        for (int i = threadIdx.x; i < nchunk; i += blockDim.x) {
+            double2 p = part[(int64_t)t * nchunk + i];
+            re += p.x;
+            im += p.y;
+        }
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sre[threadIdx.x] += sre[threadIdx.x + o];
+            sim[threadIdx.x] += sim[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[y0] = make_double2(sre[0], sim[0]);
+}
+
+// tr{g5 S(x,x)} = sum_{alpha a} g5_alpha S(x,x)_{alpha a, alpha a}
+__global__ void k_local_trace(const double2 *S, int64_t n, int l, double2 *out) {
+    double re = 0, im = 0;
+    for (int al = 0; al < 4; al++)
+        for (int a = 0; a < 3; a++) {
+            int c = 3 * al + a;
+            double2 v = S[((int64_t)c * n + l) * 12 + c];
+            double g5 = (al < 2) ? -1.0 : 1.0;
+            re += g5 * v.x;
+            im += g5 * v.y;
+        }
+    *out = make_double2(re, im);
+}
+
+}  // namespace ddp
+
+using namespace ddp;
+
+namespace {
+
+bool dev_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int ddp_contract(ddp_ctx *ctx, int kind, int domain_id, const double *S, const double *eta, int ncol,
+                            const int src[4], double *C_out) {
+    if (!ctx || !S || !C_out) return DDP_ERR_INVALID_ARG;
+    if (kind < 0 || kind > 3) return DDP_ERR_INVALID_ARG;
+    auto di = ctx->domains.find(domain_id);
+    if (di == ctx->domains.end()) return DDP_ERR_NOT_FOUND;
+    const DomainDev &d = di->second;
+    auto gi = ctx->gauges.find(d.gauge_id);
+    if (gi == ctx->gauges.end()) return DDP_ERR_NOT_FOUND;
+    const GaugeDev &g = *gi->second;
+    if (kind == DDP_CONTRACT_PSEUDO_NOISE) {
+        if (!eta || ncol < 1) return DDP_ERR_INVALID_ARG;
+    } else if (kind == DDP_CONTRACT_PION) {
+        if (ncol < 1) return DDP_ERR_INVALID_ARG;
+    } else {
+        ncol = 12;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    cudaStream_t st = ctx->stream;
+    StreamJoin sj(ctx);
+    size_t sbytes = (size_t)ncol * d.n * 12 * sizeof(double2);
+    int rc = DDP_OK;
+    void *dS = const_cast<double *>(S), *dE = const_cast<double *>(eta);
+    bool ownS = false, ownE = false;
+    void *dOut = nullptr, *dPart = nullptr;
+    int nout = (kind == DDP_CONTRACT_PSEUDO_LOCAL) ? 1 : g.L[0];
+    bool outdev = dev_ptr(C_out);
+    Item it;
+    memset(&it, 0, sizeof(it));
+    int par = 0;
+    for (int m = 0; m < 4; m++) {
+        it.o[m] = d.o[m];
+        it.e[m] = d.e[m];
+        it.L[m] = g.L[m];
+        par += d.o[m];
+    }
+    it.par_o = par & 1;
+    it.nh = (int)(d.n / 2);
+    it.ncol = ncol;
+    int slice_n = d.e[1] * d.e[2] * d.e[3];
+    int threads = (kind == DDP_CONTRACT_NUCLEON) ? 32 : 128;
+    int nchunk = (slice_n + threads - 1) / threads;
+    cudaError_t e = cudaSuccess;
+    do {
+        if (!dev_ptr(S)) {
+            if ((e = cudaMallocAsync(&dS, sbytes, st)) != cudaSuccess) break;
+            ownS = true;
+            if ((e = cudaMemcpyAsync(dS, S, sbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        }
+        if (kind == DDP_CONTRACT_PSEUDO_NOISE && !dev_ptr(eta)) {
+            if ((e = cudaMallocAsync(&dE, sbytes, st)) != cudaSuccess) break;
+            ownE = true;
+            if ((e = cudaMemcpyAsync(dE, eta, sbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        }
+        if (outdev)
+            dOut = C_out;
+        else if ((e = cudaMallocAsync(&dOut, nout * sizeof(double2), st)) != cudaSuccess)
+            break;
+        if (kind == DDP_CONTRACT_PSEUDO_LOCAL) {
+            if (!src) {
+                rc = DDP_ERR_INVALID_ARG;
+                break;
+            }
+            int k[4];
+            bool inside = true;
+            for (int m = 0; m < 4; m++) {
+                if (src[m] < 0 || src[m] >= g.L[m]) inside = false;
+                k[m] = ((src[m] - d.o[m]) % g.L[m] + g.L[m]) % g.L[m];
+                if (k[m] >= d.e[m]) inside = false;
+            }
+            if (!inside) {
+                rc = DDP_ERR_INVALID_ARG;
+                break;
+            }
+            int l = ((k[0] * d.e[1] + k[1]) * d.e[2] + k[2]) * d.e[3] + k[3];
+            k_local_trace<<<1, 1, 0, st>>>((const double2 *)dS, d.n, l, (double2 *)dOut);
+            ctx->launches++;
+        } else {
+            if ((e = cudaMallocAsync(&dPart, (size_t)d.e[0] * nchunk * sizeof(double2), st)) != cudaSuccess) break;
+            ContractArgs a;
+            a.it = it;
+            a.S = (const double2 *)dS;
+            a.eta = (const double2 *)dE;
+            a.ncol = ncol;
+            a.kind = kind;
+            a.nchunk = nchunk;
+            a.part = (double2 *)dPart;
+            size_t smem = (kind == DDP_CONTRACT_NUCLEON) ? threads * 144 * sizeof(Cplx) : 0;
+            if (smem > 48 * 1024) {
+                if ((e = cudaFuncSetAttribute(k_contract_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem)) != cudaSuccess)
+                    break;
+            }
+            dim3 grid(nchunk, d.e[0]);
+            k_contract_slice<<<grid, threads, smem, st>>>(a);
+            k_contract_final<<<g.L[0], 256, 0, st>>>(it, (const double2 *)dPart, nchunk, (double2 *)dOut);
+            ctx->launches += 2;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if (!outdev) {
+            if ((e = cudaMemcpyAsync(C_out, dOut, nout * sizeof(double2), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                break;
+        }
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    if (ownS) cudaFreeAsync(dS, st);
+    if (ownE) cudaFreeAsync(dE, st);
+    if (dOut && !outdev) cudaFreeAsync(dOut, st);
+    if (dPart) cudaFreeAsync(dPart, st);
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    if (rc) return rc;
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "contraction");
+    return DDP_OK;
+}

@@ -1,0 +1,605 @@
+// Kernels of the domain solver: the masked even-odd hopping term with fused
+// epilogues and dot products, BiCGStab vector updates, per-solve scalar
+// updates, FP64 defect-correction steps and layout conversions.
+#pragma once
+
+#include "ddp_device.cuh"
+
+namespace ddp {
+
+// ------------------------------------------------------------ solver state
+
+// Per solve (one column of one request).  Complex scalars as double2.
+struct SolveState {
+    double2 rho, alpha, omega, beta;
+    double rr;       // inner recursive |r|^2
+    double target2;  // inner stopping threshold on |r|^2
+    double bnorm2;   // |eta|^2 (FP64)
+    double rr64;     // |eta - D_Gamma x|^2 of the current outer cycle (FP64)
+    double sigma;    // |r64| of the current cycle (0: nothing to do)
+    double scale;    // 2 kappa / sigma
+    double delta;    // inner relative tolerance of the cycle
+    double tol;      // requested relative tolerance
+    double floor_delta;  // smallest useful inner tolerance of the storage format
+    int active;      // inner iteration running
+    int iters;       // inner iterations of the current cycle
+    int total_iters; // inner iterations over all cycles
+    int status;      // inner: 0 running, 1 converged, 2 breakdown, 3 iteration cap, 4 skipped
+    int outer_done;  // 1 once |eta - D x| <= tol |eta|
+    int item, col;
+    int maxit;       // inner iteration cap per cycle
+};
+
+struct LoopCtl {
+    int n_active;
+    int iter;
+    int maxit;
+    int pad;
+};
+
+// Reduction partial buffers: complex and real, per (item, column, tile).
+struct Partials {
+    double2 *c;
+    double *n;
+};
+
+enum Epi { EPI_PLAIN = 0, EPI_MHAT = 1, EPI_AXPY_K = 2, EPI_DIRAC = 3, EPI_RESID = 4 };
+enum Dot { DOT_NONE = 0, DOT_RHAT = 1, DOT_TS = 2, DOT_NORM = 3 };
+
+struct HopArgs {
+    Launch L;
+    int p;          // parity of the output sites
+    FieldView in;   // opposite-parity input
+    FieldView out;  // output (parity p)
+    FieldView v1;   // same-parity operand of the epilogue
+    FieldView v2;   // second same-parity operand (EPI_RESID: eta)
+    FieldView rh;   // shadow residual for DOT_RHAT
+    Partials part;
+};
+
+// Map a block/thread of a tile-structured launch to (item, column, site).
+struct TileCoord {
+    int col, h, tile;
+    bool valid;
+    int64_t cb;  // column base in the fields
+};
+
+__device__ __forceinline__ TileCoord tile_coord(const Item &it, const Launch &L) {
+    TileCoord t;
+    int lb = blockIdx.x - it.blk0;
+    t.tile = lb % it.ntiles;
+    int cg = lb / it.ntiles;
+    int cl = threadIdx.x / L.TS;
+    int sl = threadIdx.x - cl * L.TS;
+    t.col = cg * L.CG + cl;
+    t.h = t.tile * L.TS + sl;
+    t.valid = (t.col < it.ncol) && (t.h < it.nh) && (cl < L.CG);
+    t.cb = it.fbase + (int64_t)t.col * it.nh;
+    return t;
+}
+
+// Block reduction of (complex, real) per column: lanes of a warp share one
+// column (TS is a multiple of 32); warps of the same column are added in
+// warp order.  Fixed order: results do not depend on the batch around them.
+__device__ __forceinline__ void block_partials(const Item &it, const Launch &L, const TileCoord &tc, double cre,
+                                               double cim, double nn, Partials part, bool want_c, bool want_n) {
+    __shared__ double s_re[32], s_im[32], s_nn[32];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (want_c) {
+        cre = warp_sum(cre);
+        cim = warp_sum(cim);
+    }
+    if (want_n) nn = warp_sum(nn);
+    if (lane == 0) {
+        s_re[warp] = cre;
+        s_im[warp] = cim;
+        s_nn[warp] = nn;
+    }
+    __syncthreads();
+    int wpc = L.TS >> 5;  // warps per column
+    if ((int)threadIdx.x < L.CG) {
+        int cl = threadIdx.x;
+        int lb = blockIdx.x - it.blk0;
+        int cg = lb / it.ntiles;
+        int col = cg * L.CG + cl;
+        if (col < it.ncol) {
+            double a = 0, b = 0, c = 0;
+            for (int w = cl * wpc; w < (cl + 1) * wpc; w++) {
+                a += s_re[w];
+                b += s_im[w];
+                c += s_nn[w];
+            }
+            int64_t idx = it.pbase + (int64_t)col * it.ntiles + tc.tile;
+            if (want_c) part.c[idx] = make_double2(a, b);
+            if (want_n) part.n[idx] = c;
+        }
+    }
+}
+
+__device__ __forceinline__ void load_item(const Launch &L, Item &dst) {
+    if (threadIdx.x == 0) dst = L.items[find_item(L.items, L.nitems, blockIdx.x)];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ hopping kernel
+
+template <class P, int EPI, int DOT>
+__global__ void __launch_bounds__(512) k_hop(HopArgs a) {
+    using R = typename P::real;
+    __shared__ Item it;
+    load_item(a.L, it);
+    TileCoord tc = tile_coord(it, a.L);
+    double cre = 0, cim = 0, nn = 0;
+    if (tc.valid) {
+        cx<R> acc[4][3];
+        hop_site<P>(it, a.in, tc.cb, tc.h, a.p, acc);
+        R o[24];
+        int64_t i = tc.cb + tc.h;
+        const R kap = (R)it.kappa;
+        if (EPI == EPI_PLAIN) {
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    o[2 * (3 * s + c)] = acc[s][c].re;
+                    o[2 * (3 * s + c) + 1] = acc[s][c].im;
+                }
+        } else {
+            R w[24];
+            load_spinor<P>(a.v1, i, w);
+            R cw, ca;
+            if (EPI == EPI_MHAT) {
+                cw = R(1);
+                ca = -kap * kap;
+            } else if (EPI == EPI_AXPY_K) {
+                cw = R(1);
+                ca = kap;
+            } else if (EPI == EPI_DIRAC) {
+                cw = R(1) / (R(2) * kap);
+                ca = R(-0.5);
+            } else {  // EPI_RESID: eta - x/(2 kappa) + acc/2
+                cw = -R(1) / (R(2) * kap);
+                ca = R(0.5);
+            }
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    int j = 2 * (3 * s + c);
+                    o[j] = cw * w[j] + ca * acc[s][c].re;
+                    o[j + 1] = cw * w[j + 1] + ca * acc[s][c].im;
+                }
+            if (EPI == EPI_RESID) {
+                load_spinor<P>(a.v2, i, w);
+#pragma unroll
+                for (int j = 0; j < 24; j++) o[j] += w[j];
+            }
+            if (DOT == DOT_TS) {
+                // (t, s) = sum conj(t) s with t = out, s = v1 (reload v1: w was reused)
+                R s1[24];
+                load_spinor<P>(a.v1, i, s1);
+#pragma unroll
+                for (int j = 0; j < 12; j++) {
+                    cre += (double)(o[2 * j] * s1[2 * j] + o[2 * j + 1] * s1[2 * j + 1]);
+                    cim += (double)(o[2 * j] * s1[2 * j + 1] - o[2 * j + 1] * s1[2 * j]);
+                }
+            }
+        }
+        store_spinor<P>(a.out, i, o);
+        if (DOT == DOT_RHAT) {
+            R r[24];
+            load_spinor<P>(a.rh, i, r);
+#pragma unroll
+            for (int j = 0; j < 12; j++) {
+                cre += (double)(r[2 * j] * o[2 * j] + r[2 * j + 1] * o[2 * j + 1]);
+                cim += (double)(r[2 * j] * o[2 * j + 1] - r[2 * j + 1] * o[2 * j]);
+            }
+        }
+        if (DOT == DOT_TS || DOT == DOT_NORM) {
+            double s = 0;
+#pragma unroll
+            for (int j = 0; j < 24; j++) s += (double)(o[j] * o[j]);
+            nn = s;
+        }
+    }
+    if (DOT != DOT_NONE) block_partials(it, a.L, tc, cre, cim, nn, a.part, DOT == DOT_RHAT || DOT == DOT_TS,
+                                        DOT == DOT_TS || DOT == DOT_NORM);
+}
+
+// ------------------------------------------------------------ vector updates
+
+enum BlasOp { OP_P_UPDATE = 0, OP_S_UPDATE = 1, OP_XR_UPDATE = 2, OP_INIT = 3, OP_NORM = 4 };
+
+struct BlasArgs {
+    Launch L;
+    FieldView x, r, rh, p, v, s, t;
+    const SolveState *st;
+    Partials part;
+};
+
+template <class P, int OP>
+__global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
+    using R = typename P::real;
+    __shared__ Item it;
+    load_item(a.L, it);
+    TileCoord tc = tile_coord(it, a.L);
+    double cre = 0, cim = 0, nn = 0;
+    if (tc.valid) {
+        int64_t i = tc.cb + tc.h;
+        const SolveState &S = a.st[it.solve0 + tc.col];
+        if (OP == OP_P_UPDATE) {  // p = r + beta (p - omega v)
+            R r[24], p[24], v[24];
+            load_spinor<P>(a.r, i, r);
+            load_spinor<P>(a.p, i, p);
+            load_spinor<P>(a.v, i, v);
+            const R br = (R)S.beta.x, bi = (R)S.beta.y, wr = (R)S.omega.x, wi = (R)S.omega.y;
+#pragma unroll
+            for (int j = 0; j < 12; j++) {
+                R qr = p[2 * j] - (wr * v[2 * j] - wi * v[2 * j + 1]);
+                R qi = p[2 * j + 1] - (wr * v[2 * j + 1] + wi * v[2 * j]);
+                p[2 * j] = r[2 * j] + (br * qr - bi * qi);
+                p[2 * j + 1] = r[2 * j + 1] + (br * qi + bi * qr);
+            }
+            store_spinor<P>(a.p, i, p);
+        } else if (OP == OP_S_UPDATE) {  // s = r - alpha v
+            R r[24], v[24];
+            load_spinor<P>(a.r, i, r);
+            load_spinor<P>(a.v, i, v);
+            const R ar = (R)S.alpha.x, ai = (R)S.alpha.y;
+#pragma unroll
+            for (int j = 0; j < 12; j++) {
+                r[2 * j] -= ar * v[2 * j] - ai * v[2 * j + 1];
+                r[2 * j + 1] -= ar * v[2 * j + 1] + ai * v[2 * j];
+            }
+            store_spinor<P>(a.s, i, r);
+        } else if (OP == OP_XR_UPDATE) {  // x += alpha p + omega s ; r = s - omega t ; dots
+            R x[24], p[24], s[24], t[24];
+            load_spinor<P>(a.x, i, x);
+            load_spinor<P>(a.p, i, p);
+            load_spinor<P>(a.s, i, s);
+            load_spinor<P>(a.t, i, t);
+            const R ar = (R)S.alpha.x, ai = (R)S.alpha.y, wr = (R)S.omega.x, wi = (R)S.omega.y;
+#pragma unroll
+            for (int j = 0; j < 12; j++) {
+                x[2 * j] += (ar * p[2 * j] - ai * p[2 * j + 1]) + (wr * s[2 * j] - wi * s[2 * j + 1]);
+                x[2 * j + 1] += (ar * p[2 * j + 1] + ai * p[2 * j]) + (wr * s[2 * j + 1] + wi * s[2 * j]);
+                s[2 * j] -= wr * t[2 * j] - wi * t[2 * j + 1];
+                s[2 * j + 1] -= wr * t[2 * j + 1] + wi * t[2 * j];
+            }
+            store_spinor<P>(a.x, i, x);
+            store_spinor<P>(a.r, i, s);
+            R rh[24];
+            load_spinor<P>(a.rh, i, rh);
+            double n2 = 0;
+#pragma unroll
+            for (int j = 0; j < 12; j++) {
+                cre += (double)(rh[2 * j] * s[2 * j] + rh[2 * j + 1] * s[2 * j + 1]);
+                cim += (double)(rh[2 * j] * s[2 * j + 1] - rh[2 * j + 1] * s[2 * j]);
+                n2 += (double)(s[2 * j] * s[2 * j] + s[2 * j + 1] * s[2 * j + 1]);
+            }
+            nn = n2;
+        } else if (OP == OP_INIT) {  // rh = r ; p = r ; x = 0
+            R r[24], z[24];
+            load_spinor<P>(a.r, i, r);
+            store_spinor<P>(a.rh, i, r);
+            store_spinor<P>(a.p, i, r);
+#pragma unroll
+            for (int j = 0; j < 24; j++) z[j] = R(0);
+            store_spinor<P>(a.x, i, z);
+        } else if (OP == OP_NORM) {  // |x|^2
+            R x[24];
+            load_spinor<P>(a.x, i, x);
+            double n2 = 0;
+#pragma unroll
+            for (int j = 0; j < 24; j++) n2 += (double)(x[j] * x[j]);
+            nn = n2;
+        }
+    }
+    if (OP == OP_XR_UPDATE || OP == OP_NORM)
+        block_partials(it, a.L, tc, cre, cim, nn, a.part, OP == OP_XR_UPDATE, true);
+}
+
+// ---------------------------------------------------- FP64 <-> storage format
+
+struct ConvArgs {
+    Launch L;
+    FieldView lo;   // storage-format field
+    FieldView hi;   // FP64 field
+    const SolveState *st;
+};
+
+// lo = scale * hi  (scale = 2 kappa / sigma: the normalised defect of Sec. "mixed")
+template <class P>
+__global__ void __launch_bounds__(512) k_to_low(ConvArgs a) {
+    using R = typename P::real;
+    __shared__ Item it;
+    load_item(a.L, it);
+    TileCoord tc = tile_coord(it, a.L);
+    if (!tc.valid) return;
+    int64_t i = tc.cb + tc.h;
+    const double sc = a.st[it.solve0 + tc.col].scale;
+    double v[24];
+    load_spinor<PF64>(a.hi, i, v);
+    R w[24];
+#pragma unroll
+    for (int j = 0; j < 24; j++) w[j] = (R)(sc * v[j]);
+    store_spinor<P>(a.lo, i, w);
+}
+
+// hi += sigma * lo  (FP64 accumulation of the correction)
+template <class P>
+__global__ void __launch_bounds__(512) k_accum(ConvArgs a) {
+    using R = typename P::real;
+    __shared__ Item it;
+    load_item(a.L, it);
+    TileCoord tc = tile_coord(it, a.L);
+    if (!tc.valid) return;
+    int64_t i = tc.cb + tc.h;
+    const double sg = a.st[it.solve0 + tc.col].sigma;
+    if (sg == 0.0) return;
+    R w[24];
+    load_spinor<P>(a.lo, i, w);
+    double v[24];
+    load_spinor<PF64>(a.hi, i, v);
+#pragma unroll
+    for (int j = 0; j < 24; j++) v[j] += sg * (double)w[j];
+    store_spinor<PF64>(a.hi, i, v);
+}
+
+// ------------------------------------------------------------ scalar updates
+
+enum FinOp { FIN_BNORM = 0, FIN_RESID = 1, FIN_INIT = 2, FIN_ALPHA = 3, FIN_OMEGA = 4, FIN_RHO = 5 };
+
+struct FinArgs {
+    const Item *items;
+    SolveState *st;
+    int nsolve;
+    Partials A, B;  // B used by FIN_BNORM / FIN_RESID (odd parity)
+    LoopCtl *ctl;
+};
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// One block per solve: fixed-order sum of the solve's tile partials, then the
+// scalar recurrences of BiCGStab (van der Vorst) or of the defect correction.
+template <int FIN>
+__global__ void __launch_bounds__(256) k_fin(FinArgs a) {
+    int s = blockIdx.x;
+    if (s >= a.nsolve) return;
+    SolveState &S = a.st[s];
+    const Item &it = a.items[S.item];
+    int64_t base = it.pbase + (int64_t)S.col * it.ntiles;
+    const bool want_c = (FIN == FIN_ALPHA || FIN == FIN_OMEGA || FIN == FIN_RHO);
+    const bool two = (FIN == FIN_BNORM || FIN == FIN_RESID);
+    double cr = 0, ci = 0, nn = 0;
+    for (int t = threadIdx.x; t < it.ntiles; t += blockDim.x) {
+        if (want_c) {
+            double2 c = a.A.c[base + t];
+            cr += c.x;
+            ci += c.y;
+        }
+        if (FIN != FIN_ALPHA) nn += a.A.n[base + t];
+        if (two) nn += a.B.n[base + t];
+    }
+    __shared__ double sr[256], si[256], sn[256];
+    sr[threadIdx.x] = cr;
+    si[threadIdx.x] = ci;
+    sn[threadIdx.x] = nn;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sr[threadIdx.x] += sr[threadIdx.x + o];
+            si[threadIdx.x] += si[threadIdx.x + o];
+            sn[threadIdx.x] += sn[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double2 c = make_double2(sr[0], si[0]);
+    double n = sn[0];
+    const double2 zero = make_double2(0, 0), one = make_double2(1, 0);
+    if (FIN == FIN_BNORM) {
+        S.bnorm2 = n;
+        S.outer_done = (n == 0.0);
+    } else if (FIN == FIN_RESID) {
+        S.rr64 = n;
+        bool done = S.outer_done || (n <= S.tol * S.tol * S.bnorm2) || !(n == n);
+        S.outer_done = done ? 1 : 0;
+        if (done) {
+            S.sigma = 0;
+            S.scale = 0;
+        } else {
+            S.sigma = sqrt(n);
+            S.scale = 2.0 * it.kappa / S.sigma;
+            double d = 0.5 * S.tol * sqrt(S.bnorm2 / n);
+            d = fmax(d, S.floor_delta);
+            S.delta = fmin(d, 0.1);
+        }
+    } else if (FIN == FIN_INIT) {
+        S.rr = n;
+        S.rho = make_double2(n, 0);
+        S.target2 = S.delta * S.delta * n;
+        S.iters = 0;
+        bool act = (S.sigma > 0) && (n > 0);
+        S.active = act ? 1 : 0;
+        S.status = act ? 0 : 4;
+        S.alpha = act ? one : zero;
+        S.omega = act ? one : zero;
+        S.beta = zero;
+        if (act) atomicAdd(&a.ctl->n_active, 1);
+    } else if (FIN == FIN_ALPHA) {
+        if (S.active) {
+            if (!(c.x * c.x + c.y * c.y > 0) || !isfinite(c.x) || !isfinite(c.y)) {
+                S.active = 0;
+                S.status = 2;
+                S.alpha = zero;
+                S.omega = zero;
+                S.beta = zero;
+            } else {
+                S.alpha = cdiv(S.rho, c);
+            }
+        }
+    } else if (FIN == FIN_OMEGA) {
+        if (S.active) S.omega = (n > 0) ? cdiv(c, make_double2(n, 0)) : zero;
+    } else if (FIN == FIN_RHO) {
+        if (S.active) {
+            S.iters++;
+            S.total_iters++;
+            S.rr = n;
+            bool w0 = (S.omega.x == 0.0 && S.omega.y == 0.0);
+            if (n <= S.target2) {
+                S.active = 0;
+                S.status = 1;
+            } else if (!(c.x * c.x + c.y * c.y > 0) || w0 || !isfinite(n)) {
+                S.active = 0;
+                S.status = 2;
+            } else if (S.iters >= S.maxit) {
+                S.active = 0;
+                S.status = 3;
+            } else {
+                S.beta = cmuld(cdiv(c, S.rho), cdiv(S.alpha, S.omega));
+                S.rho = c;
+            }
+            if (!S.active) {
+                S.alpha = zero;
+                S.omega = zero;
+                S.beta = zero;
+            } else {
+                atomicAdd(&a.ctl->n_active, 1);
+            }
+        }
+    }
+}
+
+// Loop controller of the device-driven inner loop: continue while any solve
+// is active and the global iteration cap is not reached.
+static __global__ void k_loop_ctl(LoopCtl *ctl, cudaGraphConditionalHandle h) {
+    int cont = (ctl->n_active > 0) && (++ctl->iter < ctl->maxit);
+    ctl->n_active = 0;
+    cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
+// Host-polled variant (no conditional node): the same bookkeeping, the host
+// reads ctl->pad as the continue flag.
+static __global__ void k_loop_ctl_host(LoopCtl *ctl) {
+    int cont = (ctl->n_active > 0) && (++ctl->iter < ctl->maxit);
+    ctl->n_active = 0;
+    ctl->pad = cont;
+}
+
+// ---------------------------------------------- user layout <-> even-odd fields
+//
+// User spinors: [ncol][n][4][3] complex, domain-local lexicographic order.
+// One launch per item; thread per (column, site).
+
+struct PackArgs {
+    Item it;
+    const double2 *user;  // eta (pack) or NULL for a point source
+    double2 *uout;        // unpack target
+    FieldView fe, fo;     // FP64 even / odd fields
+    int src_l;            // point source local index (pack with user == NULL)
+};
+
+__device__ __forceinline__ void local_coords(const Item &it, int l, int k[4]) {
+    k[3] = l % it.e[3];
+    l /= it.e[3];
+    k[2] = l % it.e[2];
+    l /= it.e[2];
+    k[1] = l % it.e[1];
+    k[0] = l / it.e[1];
+}
+
+static __global__ void k_pack(PackArgs a) {
+    int64_t n = 2 * (int64_t)a.it.nh;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n * a.it.ncol) return;
+    int col = (int)(g / n);
+    int l = (int)(g - (int64_t)col * n);
+    int k[4];
+    local_coords(a.it, l, k);
+    int par = (a.it.par_o + k[0] + k[1] + k[2] + k[3]) & 1;
+    int64_t i = a.it.fbase + (int64_t)col * a.it.nh + (l >> 1);
+    double v[24];
+    if (a.user) {
+        const double2 *u = a.user + ((int64_t)col * n + l) * 12;
+#pragma unroll
+        for (int j = 0; j < 12; j++) {
+            double2 c = u[j];
+            v[2 * j] = c.x;
+            v[2 * j + 1] = c.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 24; j++) v[j] = 0.0;
+        if (l == a.src_l) v[2 * col] = 1.0;  // column c = 3 spin + colour is component c
+    }
+    store_spinor<PF64>(par ? a.fo : a.fe, i, v);
+}
+
+static __global__ void k_unpack(PackArgs a) {
+    int64_t n = 2 * (int64_t)a.it.nh;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n * a.it.ncol) return;
+    int col = (int)(g / n);
+    int l = (int)(g - (int64_t)col * n);
+    int k[4];
+    local_coords(a.it, l, k);
+    int par = (a.it.par_o + k[0] + k[1] + k[2] + k[3]) & 1;
+    int64_t i = a.it.fbase + (int64_t)col * a.it.nh + (l >> 1);
+    double v[24];
+    load_spinor<PF64>(par ? a.fo : a.fe, i, v);
+    double2 *u = a.uout + ((int64_t)col * n + l) * 12;
+#pragma unroll
+    for (int j = 0; j < 12; j++) u[j] = make_double2(v[2 * j], v[2 * j + 1]);
+}
+
+// Low-precision pack/unpack (for applying the low-precision stencil alone).
+template <class P>
+__global__ void k_pack_low(PackArgs a, FieldView le, FieldView lo) {
+    using R = typename P::real;
+    int64_t n = 2 * (int64_t)a.it.nh;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n * a.it.ncol) return;
+    int col = (int)(g / n);
+    int l = (int)(g - (int64_t)col * n);
+    int k[4];
+    local_coords(a.it, l, k);
+    int par = (a.it.par_o + k[0] + k[1] + k[2] + k[3]) & 1;
+    int64_t i = a.it.fbase + (int64_t)col * a.it.nh + (l >> 1);
+    const double2 *u = a.user + ((int64_t)col * n + l) * 12;
+    R v[24];
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+        double2 c = u[j];
+        v[2 * j] = (R)c.x;
+        v[2 * j + 1] = (R)c.y;
+    }
+    store_spinor<P>(par ? lo : le, i, v);
+}
+
+template <class P>
+__global__ void k_unpack_low(PackArgs a, FieldView le, FieldView lo) {
+    using R = typename P::real;
+    int64_t n = 2 * (int64_t)a.it.nh;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n * a.it.ncol) return;
+    int col = (int)(g / n);
+    int l = (int)(g - (int64_t)col * n);
+    int k[4];
+    local_coords(a.it, l, k);
+    int par = (a.it.par_o + k[0] + k[1] + k[2] + k[3]) & 1;
+    int64_t i = a.it.fbase + (int64_t)col * a.it.nh + (l >> 1);
+    R v[24];
+    load_spinor<P>(par ? lo : le, i, v);
+    double2 *u = a.uout + ((int64_t)col * n + l) * 12;
+#pragma unroll
+    for (int j = 0; j < 12; j++) u[j] = make_double2((double)v[2 * j], (double)v[2 * j + 1]);
+}
+
+}  // namespace ddp

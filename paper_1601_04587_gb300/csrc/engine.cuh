@@ -1,0 +1,474 @@
+// Solver engine: domain propagators S = D_Gamma^{-1} eta (Sec. 2, Eq. diric)
+// for a batch of independent requests.
+//
+// Outer loop (FP64 defect correction): r = eta - D_Gamma x with FP64 links and
+// vectors; stop a column when |r| <= tol |eta|.  Otherwise solve
+// (2 kappa D_Gamma) e' = 2 kappa r / |r| with the even-odd Schur complement
+//   (1 - kappa^2 H_eo H_oe) e'_e = r'_e + kappa H_eo r'_o,  e'_o = r'_o + kappa H_oe e'_e
+// by BiCGStab in the storage format P to a relative tolerance delta, and
+// accumulate x += |r| e' in FP64.
+//
+// Inner loop: every column of every request iterates together; per-column
+// scalars live on the device and the loop runs inside a CUDA graph whose
+// conditional WHILE node is driven by the device (no host round trip per
+// iteration).  Converged columns freeze (alpha = omega = 0).
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+
+#include "ddp_host.h"
+
+namespace ddp {
+
+template <class P>
+struct Engine {
+    ddp_ctx *ctx;
+    int prec;
+    Plan plan;
+    FieldView be, bo, xe, xo, re64, ro64;      // FP64
+    FieldView r, rh, p, v, s, t, xi, tmp, ro;  // storage format P
+    Partials A, B;
+    Item *d_items = nullptr;
+    SolveState *d_st = nullptr;
+    LoopCtl *d_ctl = nullptr;
+    std::vector<SolveState> h_st;
+    Launch L;
+    int threads = 0;
+    cudaGraphExec_t loop_exec = nullptr;
+    cudaGraph_t loop_graph = nullptr;
+    long launches = 0;
+
+    ~Engine() {
+        if (loop_exec) cudaGraphExecDestroy(loop_exec);
+        if (loop_graph) cudaGraphDestroy(loop_graph);
+    }
+
+    HopArgs hop_args(int par, FieldView in, FieldView out, FieldView v1, FieldView v2, FieldView rhv,
+                     Partials part) {
+        HopArgs a;
+        a.L = L;
+        a.p = par;
+        a.in = in;
+        a.out = out;
+        a.v1 = v1;
+        a.v2 = v2;
+        a.rh = rhv;
+        a.part = part;
+        return a;
+    }
+
+    template <class Q, int EPI, int DOT>
+    void hop(const HopArgs &a) {
+        k_hop<Q, EPI, DOT><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
+        launches++;
+    }
+
+    template <class Q, int OP>
+    void blas(Partials part) {
+        BlasArgs a;
+        a.L = L;
+        a.x = xi;
+        a.r = r;
+        a.rh = rh;
+        a.p = p;
+        a.v = v;
+        a.s = s;
+        a.t = t;
+        a.st = d_st;
+        a.part = part;
+        k_blas<Q, OP><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
+        launches++;
+    }
+
+    template <int FIN>
+    void fin() {
+        FinArgs a;
+        a.items = d_items;
+        a.st = d_st;
+        a.nsolve = plan.nsolve;
+        a.A = A;
+        a.B = B;
+        a.ctl = d_ctl;
+        k_fin<FIN><<<plan.nsolve, 256, 0, ctx->stream>>>(a);
+        launches++;
+    }
+
+    void norm64(FieldView f, Partials part) {
+        BlasArgs a;
+        memset(&a, 0, sizeof(a));
+        a.L = L;
+        a.x = f;
+        a.st = d_st;
+        a.part = part;
+        k_blas<PF64, OP_NORM><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
+        launches++;
+    }
+
+    void conv(bool to_low, FieldView lo, FieldView hi) {
+        ConvArgs a;
+        a.L = L;
+        a.lo = lo;
+        a.hi = hi;
+        a.st = d_st;
+        if (to_low)
+            k_to_low<P><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
+        else
+            k_accum<P><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
+        launches++;
+    }
+
+    // One BiCGStab iteration on the Schur complement (van der Vorst 1992).
+    void iteration_body() {
+        FieldView none = {nullptr, nullptr, 0};
+        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, p, tmp, none, none, none, A));      // tmp = H_oe p
+        hop<P, EPI_MHAT, DOT_RHAT>(hop_args(0, tmp, v, p, none, rh, A));           // v = p - k^2 H_eo tmp
+        fin<FIN_ALPHA>();                                                           // alpha = rho / (rh, v)
+        blas<P, OP_S_UPDATE>(A);                                                    // s = r - alpha v
+        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, s, tmp, none, none, none, A));      // tmp = H_oe s
+        hop<P, EPI_MHAT, DOT_TS>(hop_args(0, tmp, t, s, none, none, A));           // t = s - k^2 H_eo tmp
+        fin<FIN_OMEGA>();                                                           // omega = (t,s)/(t,t)
+        blas<P, OP_XR_UPDATE>(A);                                                   // x, r; (rh,r), (r,r)
+        fin<FIN_RHO>();                                                             // beta, convergence
+        blas<P, OP_P_UPDATE>(A);                                                    // p = r + beta (p - omega v)
+    }
+
+    int build_loop_graph() {
+        cudaStream_t st = ctx->stream;
+        if (ctx->prm.use_conditional) {
+            DDP_CUDA(ctx, cudaGraphCreate(&loop_graph, 0));
+            cudaGraphConditionalHandle h;
+            DDP_CUDA(ctx, cudaGraphConditionalHandleCreate(&h, loop_graph, 1, cudaGraphCondAssignDefault));
+            // the parameter union has no default constructor: build it in zeroed storage
+            alignas(cudaGraphNodeParams) unsigned char cp_buf[sizeof(cudaGraphNodeParams)];
+            memset(cp_buf, 0, sizeof(cp_buf));
+            cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_buf);
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            DDP_CUDA(ctx, cudaGraphAddNode(&node, loop_graph, nullptr, nullptr, 0, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            DDP_CUDA(ctx, cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
+                                                        cudaStreamCaptureModeThreadLocal));
+            iteration_body();
+            k_loop_ctl<<<1, 1, 0, st>>>(d_ctl, h);
+            cudaGraph_t captured;
+            cudaError_t e = cudaStreamEndCapture(st, &captured);
+            if (e != cudaSuccess) return set_cuda_error(ctx, e, "capture of the inner loop");
+            DDP_CUDA(ctx, cudaGraphInstantiate(&loop_exec, loop_graph, 0));
+        } else {
+            DDP_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < ctx->prm.host_chunk; i++) {
+                iteration_body();
+                k_loop_ctl_host<<<1, 1, 0, st>>>(d_ctl);
+            }
+            cudaError_t e = cudaStreamEndCapture(st, &loop_graph);
+            if (e != cudaSuccess) return set_cuda_error(ctx, e, "capture of the inner loop");
+            DDP_CUDA(ctx, cudaGraphInstantiate(&loop_exec, loop_graph, 0));
+        }
+        return DDP_OK;
+    }
+
+    int run_inner() {
+        // body launches per iteration: 4 hops + 4 vector updates... counted after the loop
+        const long per_iter = 11;
+        if (ctx->prm.use_conditional) {
+            DDP_CUDA(ctx, cudaGraphLaunch(loop_exec, ctx->stream));
+        } else {
+            LoopCtl hc;
+            for (int guard = 0; guard < 1 + ctx->prm.max_inner / std::max(1, ctx->prm.host_chunk); guard++) {
+                DDP_CUDA(ctx, cudaGraphLaunch(loop_exec, ctx->stream));
+                DDP_CUDA(ctx, cudaMemcpyAsync(&hc, d_ctl, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
+                DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+                if (!hc.pad) break;
+            }
+        }
+        LoopCtl hc;
+        DDP_CUDA(ctx, cudaMemcpyAsync(&hc, d_ctl, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
+        DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        launches += per_iter * (long)hc.iter;
+        return DDP_OK;
+    }
+
+    int run(std::vector<Job> &jobs, std::vector<JobInfo> &infos) {
+        const EngineParams &prm = ctx->prm;
+        make_plan(jobs, prec, prm, plan);
+        const int64_t NF = plan.nfield;
+        size_t need = 6 * field_bytes<PF64>(NF) + 9 * field_bytes<P>(NF) +
+                      2 * ((size_t)plan.npart * (sizeof(double2) + sizeof(double)) + 1024) +
+                      plan.items.size() * sizeof(Item) + plan.nsolve * sizeof(SolveState) + sizeof(LoopCtl) + 4096;
+        DDP_CUDA(ctx, ctx->ws.reserve(need));
+        Arena &a = ctx->ws;
+        a.reset();
+        be = carve_field<PF64>(a, NF);
+        bo = carve_field<PF64>(a, NF);
+        xe = carve_field<PF64>(a, NF);
+        xo = carve_field<PF64>(a, NF);
+        re64 = carve_field<PF64>(a, NF);
+        ro64 = carve_field<PF64>(a, NF);
+        r = carve_field<P>(a, NF);
+        rh = carve_field<P>(a, NF);
+        p = carve_field<P>(a, NF);
+        v = carve_field<P>(a, NF);
+        s = carve_field<P>(a, NF);
+        t = carve_field<P>(a, NF);
+        xi = carve_field<P>(a, NF);
+        tmp = carve_field<P>(a, NF);
+        ro = carve_field<P>(a, NF);
+        A.c = (double2 *)a.take(plan.npart * sizeof(double2));
+        A.n = (double *)a.take(plan.npart * sizeof(double));
+        B.c = (double2 *)a.take(plan.npart * sizeof(double2));
+        B.n = (double *)a.take(plan.npart * sizeof(double));
+        d_items = (Item *)a.take(plan.items.size() * sizeof(Item));
+        d_st = (SolveState *)a.take(plan.nsolve * sizeof(SolveState));
+        d_ctl = (LoopCtl *)a.take(sizeof(LoopCtl));
+        cudaStream_t st = ctx->stream;
+        L.items = d_items;
+        L.nitems = (int)plan.items.size();
+        L.TS = plan.TS;
+        L.CG = plan.CG;
+        threads = plan.TS * plan.CG;
+
+        h_st.assign(plan.nsolve, SolveState());
+        for (size_t i = 0; i < plan.items.size(); i++) {
+            const Item &it = plan.items[i];
+            for (int c = 0; c < it.ncol; c++) {
+                SolveState &S = h_st[it.solve0 + c];
+                memset(&S, 0, sizeof(S));
+                S.item = (int)i;
+                S.col = c;
+                S.tol = jobs[i].tol;
+                S.floor_delta = prm.floor_delta[prec];
+                S.maxit = prm.max_inner;
+                S.status = 4;
+            }
+        }
+        DDP_CUDA(ctx, cudaMemcpyAsync(d_items, plan.items.data(), plan.items.size() * sizeof(Item),
+                                      cudaMemcpyHostToDevice, st));
+        DDP_CUDA(ctx, cudaMemcpyAsync(d_st, h_st.data(), plan.nsolve * sizeof(SolveState), cudaMemcpyHostToDevice,
+                                      st));
+        LoopCtl c0 = {0, 0, prm.max_inner, 0};
+        DDP_CUDA(ctx, cudaMemcpyAsync(d_ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+
+        // sources and |eta|^2
+        for (size_t i = 0; i < jobs.size(); i++) {
+            PackArgs pa;
+            memset(&pa, 0, sizeof(pa));
+            pa.it = plan.items[i];
+            pa.user = (const double2 *)jobs[i].eta;
+            pa.fe = be;
+            pa.fo = bo;
+            pa.src_l = jobs[i].src_l;
+            int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
+            k_pack<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(pa);
+            launches++;
+        }
+        norm64(be, A);
+        norm64(bo, B);
+        fin<FIN_BNORM>();
+        DDP_CUDA(ctx, cudaMemsetAsync(xe.p, 0, (size_t)NF * sizeof(double2) * 12, st));
+        DDP_CUDA(ctx, cudaMemsetAsync(xo.p, 0, (size_t)NF * sizeof(double2) * 12, st));
+        DDP_CUDA(ctx, cudaGetLastError());
+
+        int rc = build_loop_graph();
+        if (rc) return rc;
+
+        FieldView none = {nullptr, nullptr, 0};
+        int cycles = 0;
+        bool all_done = false;
+        for (int cyc = 0; cyc <= prm.max_outer; cyc++) {
+            // r64 = eta - D_Gamma x  (FP64 links, FP64 vectors)
+            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A));
+            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B));
+            fin<FIN_RESID>();
+            DDP_CUDA(ctx, cudaMemcpyAsync(h_st.data(), d_st, plan.nsolve * sizeof(SolveState),
+                                          cudaMemcpyDeviceToHost, st));
+            DDP_CUDA(ctx, cudaStreamSynchronize(st));
+            all_done = true;
+            for (auto &S : h_st) all_done = all_done && S.outer_done;
+            if (all_done || cyc == prm.max_outer) break;
+            cycles++;
+            // normalised defect in storage format, even-odd right-hand side
+            conv(true, s, re64);
+            conv(true, ro, ro64);
+            hop<P, EPI_AXPY_K, DOT_NORM>(hop_args(0, ro, r, s, none, none, A));  // r = r'_e + k H_eo r'_o
+            blas<P, OP_INIT>(A);
+            DDP_CUDA(ctx, cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), st));
+            fin<FIN_INIT>();
+            DDP_CUDA(ctx, cudaGetLastError());
+            rc = run_inner();
+            if (rc) return rc;
+            hop<P, EPI_AXPY_K, DOT_NONE>(hop_args(1, xi, tmp, ro, none, none, A));  // e'_o = r'_o + k H_oe e'_e
+            conv(false, xi, xe);
+            conv(false, tmp, xo);
+        }
+        // results
+        for (size_t i = 0; i < jobs.size(); i++) {
+            PackArgs pa;
+            memset(&pa, 0, sizeof(pa));
+            pa.it = plan.items[i];
+            pa.uout = (double2 *)jobs[i].out;
+            pa.fe = xe;
+            pa.fo = xo;
+            int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
+            k_unpack<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(pa);
+            launches++;
+        }
+        DDP_CUDA(ctx, cudaGetLastError());
+        DDP_CUDA(ctx, cudaStreamSynchronize(st));
+        infos.assign(jobs.size(), JobInfo());
+        for (size_t i = 0; i < jobs.size(); i++) {
+            const Item &it = plan.items[i];
+            JobInfo &inf = infos[i];
+            inf.outer = cycles;
+            inf.relres.resize(it.ncol);
+            bool ok = true;
+            int inner = 0;
+            for (int c = 0; c < it.ncol; c++) {
+                const SolveState &S = h_st[it.solve0 + c];
+                double rr = (S.bnorm2 > 0) ? sqrt(S.rr64 / S.bnorm2) : 0.0;
+                inf.relres[c] = rr;
+                ok = ok && (rr <= jobs[i].tol);
+                inner = std::max(inner, S.total_iters);
+            }
+            inf.inner = inner;
+            inf.status = ok ? DDP_OK : DDP_ERR_NOT_CONVERGED;
+        }
+        ctx->launches += launches;
+        return DDP_OK;
+    }
+};
+
+template <class P>
+int solve_jobs(ddp_ctx *ctx, int prec, std::vector<Job> &jobs, std::vector<JobInfo> &infos) {
+    Engine<P> eng;
+    eng.ctx = ctx;
+    eng.prec = prec;
+    return eng.run(jobs, infos);
+}
+
+// out = D_Gamma psi with the stencil of storage format P (App. A, Sec. 2).
+template <class P>
+int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *out, int prec) {
+    std::vector<Job> jobs(1, job);
+    Plan plan;
+    make_plan(jobs, prec, ctx->prm, plan);
+    const int64_t NF = plan.nfield;
+    size_t need = 4 * field_bytes<P>(NF) + sizeof(Item) + 1024;
+    DDP_CUDA(ctx, ctx->scratch.reserve(need));
+    Arena &a = ctx->scratch;
+    a.reset();
+    FieldView ie = carve_field<P>(a, NF), io = carve_field<P>(a, NF);
+    FieldView oe = carve_field<P>(a, NF), oo = carve_field<P>(a, NF);
+    Item *d_items = (Item *)a.take(sizeof(Item));
+    cudaStream_t st = ctx->stream;
+    DDP_CUDA(ctx, cudaMemcpyAsync(d_items, plan.items.data(), sizeof(Item), cudaMemcpyHostToDevice, st));
+    PackArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.it = plan.items[0];
+    pa.user = (const double2 *)psi;
+    pa.uout = (double2 *)out;
+    int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
+    unsigned nb = (unsigned)((nt + 255) / 256);
+    k_pack_low<P><<<nb, 256, 0, st>>>(pa, ie, io);
+    Launch L;
+    L.items = d_items;
+    L.nitems = 1;
+    L.TS = plan.TS;
+    L.CG = plan.CG;
+    FieldView none = {nullptr, nullptr, 0};
+    HopArgs h;
+    h.L = L;
+    h.v2 = none;
+    h.rh = none;
+    h.part.c = nullptr;
+    h.part.n = nullptr;
+    h.p = 0;
+    h.in = io;
+    h.out = oe;
+    h.v1 = ie;
+    k_hop<P, EPI_DIRAC, DOT_NONE><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
+    h.p = 1;
+    h.in = ie;
+    h.out = oo;
+    h.v1 = io;
+    k_hop<P, EPI_DIRAC, DOT_NONE><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
+    k_unpack_low<P><<<nb, 256, 0, st>>>(pa, oe, oo);
+    ctx->launches += 4;
+    DDP_CUDA(ctx, cudaGetLastError());
+    return DDP_OK;
+}
+
+// Timing of the inner-loop stencil kernel v = p - kappa^2 H_eo tmp with the
+// fused (rh, v) partials, on fields of the given domain (contents: a packed
+// unit source, which does not change the kernel's work).  Algorithmic bytes
+// per launch: input half-field, epilogue operand, shadow residual and output
+// (4 x 24 reals per site-column) plus every link of the domain once.
+template <class P>
+int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, double *bytes) {
+    std::vector<Job> jobs(1, job);
+    Plan plan;
+    make_plan(jobs, prec, ctx->prm, plan);
+    const int64_t NF = plan.nfield;
+    size_t need = 4 * field_bytes<P>(NF) + 2 * ((size_t)plan.npart * 24 + 1024) + sizeof(Item) + 1024;
+    DDP_CUDA(ctx, ctx->scratch.reserve(need));
+    Arena &a = ctx->scratch;
+    a.reset();
+    FieldView in = carve_field<P>(a, NF), v1 = carve_field<P>(a, NF), rhv = carve_field<P>(a, NF),
+              out = carve_field<P>(a, NF);
+    Partials A;
+    A.c = (double2 *)a.take(plan.npart * sizeof(double2));
+    A.n = (double *)a.take(plan.npart * sizeof(double));
+    Item *d_items = (Item *)a.take(sizeof(Item));
+    cudaStream_t st = ctx->stream;
+    DDP_CUDA(ctx, cudaMemcpyAsync(d_items, plan.items.data(), sizeof(Item), cudaMemcpyHostToDevice, st));
+    size_t fb = (size_t)NF * sizeof(typename P::chunk) * P::NCH;
+    DDP_CUDA(ctx, cudaMemsetAsync(in.p, 0, fb, st));
+    DDP_CUDA(ctx, cudaMemsetAsync(v1.p, 0, fb, st));
+    DDP_CUDA(ctx, cudaMemsetAsync(rhv.p, 0, fb, st));
+    if (P::SCALED) {
+        DDP_CUDA(ctx, cudaMemsetAsync(in.scale, 0, NF * sizeof(float), st));
+        DDP_CUDA(ctx, cudaMemsetAsync(v1.scale, 0, NF * sizeof(float), st));
+        DDP_CUDA(ctx, cudaMemsetAsync(rhv.scale, 0, NF * sizeof(float), st));
+    }
+    Launch L;
+    L.items = d_items;
+    L.nitems = 1;
+    L.TS = plan.TS;
+    L.CG = plan.CG;
+    HopArgs h;
+    FieldView none = {nullptr, nullptr, 0};
+    h.L = L;
+    h.p = 0;
+    h.in = in;
+    h.out = out;
+    h.v1 = v1;
+    h.v2 = none;
+    h.rh = rhv;
+    h.part = A;
+    cudaEvent_t e0, e1;
+    DDP_CUDA(ctx, cudaEventCreate(&e0));
+    DDP_CUDA(ctx, cudaEventCreate(&e1));
+    for (int i = 0; i < 3; i++) k_hop<P, EPI_MHAT, DOT_RHAT><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
+    DDP_CUDA(ctx, cudaEventRecord(e0, st));
+    for (int i = 0; i < iters; i++) k_hop<P, EPI_MHAT, DOT_RHAT><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
+    DDP_CUDA(ctx, cudaEventRecord(e1, st));
+    DDP_CUDA(ctx, cudaEventSynchronize(e1));
+    float t = 0;
+    DDP_CUDA(ctx, cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->launches += 3 + iters;
+    *ms = t / iters;
+    double site_cols = (double)plan.items[0].nh * job.ncol;
+    double spinor = (double)sizeof(typename P::chunk) * P::NCH + (P::SCALED ? 4.0 : 0.0);
+    double link = P::IS64 ? 144.0 : (double)sizeof(typename P::chunk) * 0 + (std::is_same<P, PF32>::value ? 48.0 : 24.0);
+    // every link touching the output parity: 8 per output site (4 forward + 4 backward)
+    *bytes = site_cols * 4.0 * spinor + (double)plan.items[0].nh * 8.0 * link;
+    return DDP_OK;
+}
+
+}  // namespace ddp

@@ -1,0 +1,294 @@
+"""CUDA path against the FP64 oracle, through the C ABI (GPU required).
+
+Tolerances: index maps and series terms bit-exact; FP64 stencil 1e-13
+relative L2 per column (summation order only); low-precision stencils at the
+rounding level of their storage (FP32 1e-6, FP16 per-site scaled 4e-3, BF16
+3e-2); propagator columns 1e-8 relative L2 at solver residual 1e-10 against
+the oracle at 1e-12; correlators 1e-7 relative L2 over time slices.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+AP = oracle.BC_ANTIPERIODIC
+
+COL_TOL = 1e-8
+CORR_TOL = 1e-7
+
+
+@pytest.fixture(scope="module")
+def ddp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_04587_gb300 import build
+    build.build()
+    import paper_1601_04587_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(ddp):
+    c = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    ddp.ddp_destroy(c)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _col_errors(got, ref):
+    return [_rel(got[c], ref[c]) for c in range(ref.shape[0])]
+
+
+LAT = (8, 4, 4, 6)
+
+
+@pytest.fixture(scope="module")
+def field(ddp, ctx):
+    U = synth.gauge_field(LAT, seed=1234)
+    gid = ddp.ddp_load_gauge(ctx, torch.from_numpy(U).cuda(), LAT, ddp.DDP_BC_ANTIPERIODIC)
+    return U, gid
+
+
+BOXES = [((0, 0, 0, 0), LAT),                    # whole lattice
+         ((6, 0, 0, 0), (4, 4, 4, 6)),           # time slab across the antiperiodic boundary
+         ((5, 1, 3, 2), (3, 2, 3, 4)),           # Dirichlet in every direction, wrapped, odd extents
+         ((2, 3, 0, 5), (5, 4, 2, 2)),
+         ((1, 0, 0, 0), (8, 4, 4, 6))]           # full extent, shifted origin
+
+
+# ------------------------------------------------------------------ index maps
+
+@pytest.mark.parametrize("box", BOXES)
+def test_domain_maps_bit_exact(ddp, ctx, field, box):
+    U, gid = field
+    o, e = box
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    gi = np.zeros(n, dtype=np.int64)
+    eo = np.zeros(n, dtype=np.int64)
+    assert ddp.ddp_domain_sites(ctx, did, gi, eo) == n
+    rg, reo, _ = oracle.domain_maps(LAT, o, e)
+    assert np.array_equal(gi, rg)
+    assert np.array_equal(eo, reo)
+
+
+def test_odd_innermost_extent_rejected(ddp, ctx, field):
+    U, gid = field
+    with pytest.raises(ddp.DDPError) as ei:
+        ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), (4, 4, 4, 3))
+    assert ei.value.status == ddp.DDP_ERR_UNSUPPORTED
+
+
+# -------------------------------------------------------------------- stencil
+
+@pytest.mark.parametrize("box", BOXES)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 1e-6), (2, 4e-3), (3, 3e-2)])
+def test_apply_dirac(ddp, ctx, field, box, prec, tol):
+    U, gid = field
+    o, e = box
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    psi = synth.random_spinor(3, n, 17)
+    ref = oracle.apply_dirac(U, LAT, AP, o, e, 0.1315, psi)
+    out = torch.zeros((3, n, 4, 3), dtype=torch.complex128, device="cuda")
+    ddp.ddp_apply_dirac(ctx, did, 0.1315, torch.from_numpy(psi).cuda(), out, 3, prec)
+    errs = _col_errors(out.cpu().numpy(), ref)
+    assert max(errs) < tol, errs
+
+
+@pytest.mark.parametrize("bc", [0, 2])
+def test_apply_dirac_other_time_boundaries(ddp, ctx, bc):
+    U = synth.gauge_field(LAT, seed=77)
+    gid = ddp.ddp_load_gauge(ctx, torch.from_numpy(U).cuda(), LAT, bc)
+    for o, e in BOXES[:3]:
+        did = ddp.ddp_set_domain(ctx, gid, o, e)
+        n = int(np.prod(e))
+        psi = synth.random_spinor(1, n, 3)
+        ref = oracle.apply_dirac(U, LAT, bc, o, e, 0.12, psi)
+        out = np.zeros_like(psi)
+        ddp.ddp_apply_dirac(ctx, did, 0.12, psi, out, 1, 0)   # host buffers
+        assert _rel(out, ref) < 1e-13
+
+
+# ----------------------------------------------------------------- propagators
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("box,src", [(BOXES[0], (0, 0, 0, 0)), (BOXES[1], (7, 1, 2, 3)),
+                                     (BOXES[2], (6, 2, 0, 5)), (BOXES[3], (4, 3, 1, 0))])
+def test_solve_propagator(ddp, ctx, field, prec, box, src):
+    U, gid = field
+    o, e = box
+    kappa = 0.124
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    ref, _, rr, st = oracle.propagator(U, LAT, AP, o, e, kappa, src, tol=1e-12)
+    assert st == 0
+    S = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
+    rc, info = ddp.ddp_solve_propagator(ctx, did, kappa, 0.0, src, 1e-10, prec, S)
+    assert rc == ddp.DDP_OK, ddp.info_dict(info)
+    assert info.max_rel_residual <= 1e-10
+    errs = _col_errors(S.cpu().numpy(), ref)
+    assert max(errs) < COL_TOL, errs
+
+
+def test_solve_sources_host_buffers(ddp, ctx, field):
+    U, gid = field
+    o, e = BOXES[1]
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    eta = synth.random_spinor(5, n, 8)
+    ref, _, rr, st = oracle.solve(U, LAT, AP, o, e, 0.125, eta, tol=1e-12)
+    out = np.zeros_like(eta)
+    rc, info = ddp.ddp_solve_sources(ctx, did, 0.125, 0.0, eta, 5, 1e-10, ddp.DDP_PREC_MIXED_FP32, out)
+    assert rc == ddp.DDP_OK
+    assert max(_col_errors(out, ref)) < COL_TOL
+
+
+def test_batch_equals_individual_solves(ddp, ctx, field):
+    """One batched launch over uneven domains gives bit-identical columns to the
+    same requests solved one by one (fixed-order per-request reductions)."""
+    U, gid = field
+    reqs, outs, alone = [], [], []
+    specs = [(BOXES[1], (7, 1, 2, 3), 0.124), (BOXES[2], (6, 2, 0, 5), 0.12), (BOXES[0], (3, 3, 3, 3), 0.122)]
+    for (o, e), src, kappa in specs:
+        did = ddp.ddp_set_domain(ctx, gid, o, e)
+        n = int(np.prod(e))
+        out = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
+        outs.append(out)
+        reqs.append(ddp.make_req(did, kappa, src, 1e-10, out))
+        one = torch.zeros_like(out)
+        ddp.ddp_solve_propagator(ctx, did, kappa, 0.0, src, 1e-10, ddp.DDP_PREC_MIXED_FP32, one)
+        alone.append(one)
+    rc, infos = ddp.ddp_solve_batch(ctx, reqs, ddp.DDP_PREC_MIXED_FP32)
+    assert rc == ddp.DDP_OK
+    for out, one, ((o, e), src, kappa) in zip(outs, alone, specs):
+        ref, *_ = oracle.propagator(U, LAT, AP, o, e, kappa, src, tol=1e-12)
+        assert max(_col_errors(out.cpu().numpy(), ref)) < COL_TOL
+        # per-request reductions in a fixed order: the batch does not change a bit
+        assert torch.equal(out, one)
+
+
+def test_not_converged_reported(ddp, ctx, field):
+    U, gid = field
+    did = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), LAT)
+    n = int(np.prod(LAT))
+    S = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
+    ddp.ddp_set_param(ctx, "max_outer", 1)
+    ddp.ddp_set_param(ctx, "max_inner", 3)
+    try:
+        rc, info = ddp.ddp_solve_propagator(ctx, did, 0.124, 0.0, (0, 0, 0, 0), 1e-10, 1, S)
+    finally:
+        ddp.ddp_set_param(ctx, "max_outer", 40)
+        ddp.ddp_set_param(ctx, "max_inner", 30000)
+    assert rc == ddp.DDP_ERR_NOT_CONVERGED
+    assert info.max_rel_residual > 1e-10
+    assert np.isfinite(S.cpu().numpy()).all()
+
+
+def test_invalid_arguments(ddp, ctx, field):
+    U, gid = field
+    did = ddp.ddp_set_domain(ctx, gid, BOXES[1][0], BOXES[1][1])
+    n = int(np.prod(BOXES[1][1]))
+    S = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ddp.DDPError) as ei:
+        ddp.ddp_solve_propagator(ctx, did, 0.12, 0.5, (7, 0, 0, 0), 1e-10, 0, S)
+    assert ei.value.status == ddp.DDP_ERR_UNSUPPORTED      # clover term
+    with pytest.raises(ddp.DDPError) as ei:
+        ddp.ddp_solve_propagator(ctx, did, 0.12, 0.0, (3, 0, 0, 0), 1e-10, 0, S)
+    assert ei.value.status == ddp.DDP_ERR_INVALID_ARG      # source outside the domain
+    bad = U.copy()
+    bad[2, 5, 1, 1] = np.nan
+    with pytest.raises(ddp.DDPError) as ei:
+        ddp.ddp_load_gauge(ctx, bad, LAT, 1)
+    assert ei.value.status == ddp.DDP_ERR_INVALID_ARG
+    nonunitary = U.copy()
+    nonunitary[0, 0] *= 1.01
+    with pytest.raises(ddp.DDPError):
+        ddp.ddp_load_gauge(ctx, nonunitary, LAT, 1)
+    with pytest.raises(ddp.DDPError):
+        ddp.ddp_load_gauge(ctx, U, (8, 4, 4, 5), 1)
+
+
+# ------------------------------------------------------------- series + contractions
+
+def test_series_terms_bit_exact(ddp, ctx, field):
+    U, gid = field
+    src = (7, 1, 2, 3)
+    small, big = ((6, 0, 0, 0), (4, 4, 4, 6)), ((5, 0, 0, 0), (6, 4, 4, 6))
+    ds = ddp.ddp_set_domain(ctx, gid, *small)
+    db = ddp.ddp_set_domain(ctx, gid, *big)
+    Ss, *_ = oracle.propagator(U, LAT, AP, *small, 0.124, src)
+    Sb, *_ = oracle.propagator(U, LAT, AP, *big, 0.124, src)
+    T = torch.zeros(Sb.shape, dtype=torch.complex128, device="cuda")
+    ddp.ddp_series_terms(ctx, ds, torch.from_numpy(Ss).cuda(), db, torch.from_numpy(Sb).cuda(), T, 12)
+    ref = oracle.series_term(LAT, small[0], small[1], Ss, big[0], big[1], Sb)
+    assert np.array_equal(T.cpu().numpy(), ref)
+
+
+def test_series_rejects_non_nested(ddp, ctx, field):
+    U, gid = field
+    ds = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), (4, 4, 4, 6))
+    db = ddp.ddp_set_domain(ctx, gid, (2, 0, 0, 0), (4, 4, 4, 6))
+    S = np.zeros((12, 384, 4, 3), dtype=np.complex128)
+    with pytest.raises(ddp.DDPError):
+        ddp.ddp_series_terms(ctx, ds, S, db, S.copy(), S.copy(), 12)
+
+
+@pytest.mark.parametrize("box,src", [(BOXES[0], (0, 0, 0, 0)), (BOXES[1], (7, 1, 2, 3)), (BOXES[2], (6, 2, 0, 5))])
+def test_contractions(ddp, ctx, field, box, src):
+    U, gid = field
+    o, e = box
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    S, *_ = oracle.propagator(U, LAT, AP, o, e, 0.124, src)
+    Sd = torch.from_numpy(S).cuda()
+    C = np.zeros(2 * LAT[0])
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_NUCLEON, did, Sd, C)
+    want = oracle.nucleon(LAT, o, e, S)
+    assert _rel(C[0::2] + 1j * C[1::2], want) < CORR_TOL
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PION, did, Sd, C)
+    assert _rel(C[0::2], oracle.pion(LAT, o, e, S)) < CORR_TOL
+    assert np.all(C[1::2] == 0)
+    c1 = np.zeros(2)
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_LOCAL, did, Sd, c1, src=src)
+    t = oracle.local_trace(LAT, o, e, S, src)
+    assert abs(complex(c1[0], c1[1]) - t) <= CORR_TOL * abs(t)
+    n = int(np.prod(e))
+    eta = synth.diluted_noise_columns(synth.noise_field(n, 5))
+    psi, *_ = oracle.solve(U, LAT, AP, o, e, 0.124, eta)
+    Cd = torch.zeros(2 * LAT[0], dtype=torch.float64, device="cuda")
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_NOISE, did, torch.from_numpy(psi).cuda(), Cd,
+                     eta=torch.from_numpy(eta).cuda(), ncol=12)
+    Cn = Cd.cpu().numpy()
+    assert _rel(Cn[0::2] + 1j * Cn[1::2], oracle.noise_trace(LAT, o, e, eta, psi)) < CORR_TOL
+
+
+def test_gauge_region_variant(ddp, ctx, field):
+    """A variant gauge field (links of one region replaced) solves like a
+    freshly loaded field with the same links."""
+    U, gid = field
+    Uv = synth.variant_field(U, LAT, 0, 4, seed=9)
+    o, e = (0, 0, 0, 0), (4, 4, 4, 6)
+    gi, _, _ = oracle.domain_maps(LAT, o, e)
+    Ubox = np.ascontiguousarray(Uv[:, gi])
+    vid = ddp.ddp_load_gauge_region(ctx, gid, o, e, torch.from_numpy(Ubox).cuda())
+    fid = ddp.ddp_load_gauge(ctx, torch.from_numpy(Uv).cuda(), LAT, 1)
+    psi = synth.random_spinor(1, int(np.prod(LAT)), 2)
+    outs = []
+    for g in (vid, fid):
+        did = ddp.ddp_set_domain(ctx, g, (0, 0, 0, 0), LAT)
+        out = np.zeros_like(psi)
+        ddp.ddp_apply_dirac(ctx, did, 0.12, psi, out, 1, 0)
+        outs.append(out)
+        ddp.ddp_free_domain(ctx, did)
+    assert np.array_equal(outs[0], outs[1])
+    ref = oracle.apply_dirac(Uv, LAT, AP, (0, 0, 0, 0), LAT, 0.12, psi)
+    assert _rel(outs[0], ref) < 1e-13
+    ddp.ddp_free_gauge(ctx, vid)
+    ddp.ddp_free_gauge(ctx, fid)
