@@ -1,0 +1,371 @@
+"""Benchmark of the domain-propagator hot path on GB300.
+
+Workload (default): a 48 x 24^3 lattice (antiperiodic in time, periodic in
+space) with the seeded synthetic SU(3) field of plaquette 0.59, nested time
+slabs of thickness 8, 16, 24 around a point source at the origin plus the
+full lattice; per step:
+  a1 load + pack the gauge field (from a device copy),
+  a3-a5 the four 12-column domain propagators S^(0), S^(1), S^(2), S to a
+        true FP64 residual of 1e-10 in one batched solve,
+  a6 the three series terms S^(i) - S^(i-1) and S - S^(2),
+  a7 nucleon and pion correlators of each propagator and tr{g5 S(x,x)}.
+`value` counts domain-propagator solves (12 columns each) per second with
+inputs resident in HBM; `e2e` runs the same step through the C ABI with host
+buffers (pinned), every transfer inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp16]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+L = synth.SLAB_LATTICE
+THICK = synth.SLAB_THICKNESS
+# kappa of the benchmark: the stated 0.1550 lies beyond the critical point of
+# the i.i.d. synthetic ensemble (BiCGStab diverges on the 16, 24 and full
+# domains), 0.1400 is the largest value on a 0.005 grid at which every domain
+# of the workload converges.
+KAPPA = 0.1400
+TOL = 1e-10
+SRC = (0, 0, 0, 0)
+METRIC = "domain-propagator solves/s (12 columns, true FP64 residual 1e-10)"
+UNIT = "solves/s"
+
+
+def boxes():
+    out = [synth.centered_time_slab(L, t, 0) for t in THICK]
+    out.append(synth.Box((0, 0, 0, 0), L))
+    return out
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def hop_traffic_record():
+    """ncu DRAM bytes per launch of the stencil kernel, if the committed record
+    matches the current kernel sources."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "hop_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        rec = json.load(open(p))
+        h = hashlib.sha256()
+        for f in ("ddp_device.cuh", "ddp_kernels.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_1601_04587_gb300", "csrc", f), "rb").read())
+        if rec.get("sources_sha256") != h.hexdigest():
+            return None
+        return rec
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = str(device_index)
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.dev, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+class Workload:
+    def __init__(self, ddp, torch, ctx, precision, U):
+        self.ddp, self.torch, self.ctx, self.prec = ddp, torch, ctx, precision
+        self.U_dev = torch.from_numpy(U).cuda()
+        self.bx = boxes()
+        self.outs = [torch.zeros((12, b.n_sites, 4, 3), dtype=torch.complex128, device="cuda") for b in self.bx]
+        self.terms = [torch.zeros_like(o) for o in self.outs[1:]]
+        self.C = torch.zeros((len(self.bx), 2, 2 * L[0]), dtype=torch.float64, device="cuda")
+        self.trace = torch.zeros((len(self.bx), 2), dtype=torch.float64, device="cuda")
+        self.infos = None
+
+    def step(self, host=None):
+        """One pass of the hot path.  host: pinned host buffers for the e2e variant."""
+        ddp, ctx = self.ddp, self.ctx
+        U = self.U_dev if host is None else host["U"]
+        outs = self.outs if host is None else host["S"]
+        terms = self.terms if host is None else host["T"]
+        C = self.C if host is None else host["C"]
+        tr = self.trace if host is None else host["tr"]
+        gid = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
+        dids = [ddp.ddp_set_domain(ctx, gid, b.origin, b.extent) for b in self.bx]
+        reqs = [ddp.make_req(d, KAPPA, SRC, TOL, o) for d, o in zip(dids, outs)]
+        rc, self.infos = ddp.ddp_solve_batch(ctx, reqs, self.prec)
+        for i in range(1, len(dids)):
+            ddp.ddp_series_terms(ctx, dids[i - 1], outs[i - 1], dids[i], outs[i], terms[i - 1], 12)
+        for i, d in enumerate(dids):
+            ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_NUCLEON, d, outs[i], C[i, 0])
+            ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PION, d, outs[i], C[i, 1])
+            ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_LOCAL, d, outs[i], tr[i], src=SRC)
+        for d in dids:
+            ddp.ddp_free_domain(ctx, d)
+        ddp.ddp_free_gauge(ctx, gid)
+        return rc
+
+    def host_buffers(self):
+        t = self.torch
+        h = {"U": t.from_numpy(np.ascontiguousarray(self.U_dev.cpu().numpy())).pin_memory(),
+             "S": [t.zeros(o.shape, dtype=o.dtype).pin_memory() for o in self.outs],
+             "T": [t.zeros(o.shape, dtype=o.dtype).pin_memory() for o in self.terms],
+             "C": t.zeros(self.C.shape, dtype=t.float64).pin_memory(),
+             "tr": t.zeros(self.trace.shape, dtype=t.float64).pin_memory()}
+        nb = lambda x: x.numel() * x.element_size()  # noqa: E731
+        S = sum(nb(x) for x in h["S"])
+        T = sum(nb(x) for x in h["T"])
+        # H2D: gauge field, both propagators of every series term, every contraction input
+        h2d = nb(h["U"]) + sum(nb(h["S"][i - 1]) + nb(h["S"][i]) for i in range(1, 4)) + 3 * S
+        d2h = S + T + nb(h["C"]) + nb(h["tr"])
+        return h, h2d, d2h
+
+
+def timed(torch, fn, steps, dist=None):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record()
+    for _ in range(steps):
+        fn()
+    end.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return start.elapsed_time(end) / 1e3
+
+
+def cpu_oracle_sample(U, kappa):
+    """The FP64 oracle, as it stands, on one column of each of the two thinnest
+    slabs: 2 of the step's 48 column-solves, i.e. 1/6 of a step's 4 solves per
+    12 columns -> (2/12) propagator solves."""
+    import oracle
+    t0 = time.perf_counter()
+    for b in boxes()[:2]:
+        n = b.n_sites
+        eta = np.zeros((1, n, 4, 3), dtype=np.complex128)
+        eta[0, oracle.local_index(L, b.origin, b.extent, SRC), 0, 0] = 1.0
+        oracle.solve(U, L, oracle.BC_ANTIPERIODIC, b.origin, b.extent, kappa, eta, tol=TOL)
+    dt = time.perf_counter() - t0
+    return (2.0 / 12.0) / dt, dt
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1601_04587_gb300 as ddp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    prec = ddp.PRECISIONS[args.precision]
+    U = synth.gauge_field(L, seed=synth.SEED_GAUGE + rank)
+    ctx = ddp.ddp_create(torch.cuda.current_device(), torch.cuda.current_stream().cuda_stream)
+    wl = Workload(ddp, torch, ctx, prec, U)
+    for _ in range(args.warmup):
+        wl.step()
+    launches0 = ddp.ddp_kernel_launches(ctx)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    secs = timed(torch, wl.step, args.steps, dist)
+    clk = clocks.stop()
+    launches = ddp.ddp_kernel_launches(ctx) - launches0
+    infos = [ddp.info_dict(i) for i in wl.infos]
+    # slowest rank decides
+    if dist:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    nsolve = len(wl.bx) * args.steps * world
+    value = nsolve / secs
+
+    # end to end: host buffers through the C ABI, transfers inside the timed region
+    host, h2d, d2h = wl.host_buffers()
+    wl.step(host)
+    e2e_secs = timed(torch, lambda: wl.step(host), max(1, args.steps // 2), dist)
+    if dist:
+        t = torch.tensor([e2e_secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_secs = float(t.item())
+    e2e_value = len(wl.bx) * max(1, args.steps // 2) * world / e2e_secs
+
+    # plain FP64 GPU path on the same workload
+    fp64 = None
+    if not args.skip_fp64 and prec != ddp.DDP_PREC_FP64:
+        wl64 = Workload(ddp, torch, ctx, ddp.DDP_PREC_FP64, U)
+        wl64.step()
+        s64 = timed(torch, wl64.step, 1, dist)
+        fp64 = {"solves_per_s": len(wl.bx) / s64, "ms_per_step": 1e3 * s64,
+                "max_rel_residual": max(i.max_rel_residual for i in wl64.infos)}
+        del wl64
+
+    # roofline of the dominant kernel: the inner-loop Schur-complement stencil
+    gid = ddp.ddp_load_gauge(ctx, wl.U_dev, L, ddp.DDP_BC_ANTIPERIODIC)
+    did = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), L)
+    ms, algo_bytes = ddp.ddp_time_hop(ctx, did, KAPPA, 12, prec, 50)
+    ddp.ddp_free_domain(ctx, did)
+    ddp.ddp_free_gauge(ctx, gid)
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / (ms * 1e-3) / 1e9
+    rec = hop_traffic_record()
+    traffic = None
+    if rec and rec.get("precision") == args.precision:
+        traffic = rec.get("dram_bytes_per_launch_full")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16",
+                                                           "bf16": "bf16"}[args.precision],
+        "data": "synthetic (seeded SU(3) field, plaquette 0.59)",
+        "config": {"workload": f"48x24^3 nested time slabs 8/16/24 + full lattice, 12-column point-source "
+                               f"propagators, kappa {KAPPA}, tol {TOL}",
+                   "lattice": list(L), "kappa": KAPPA, "kappa_stated": 0.155, "tol": TOL,
+                   "precision": f"mixed: FP32 inner on {args.precision} storage, FP64 defect correction"
+                   if prec else "fp64",
+                   "l2": "inputs larger than L2 (links 0.38 GB FP64, propagators 3.1 GB)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": f"k_hop<{args.precision}, MHAT, RHAT>",
+                     "ms_per_launch": ms, "algorithmic_bytes_per_launch": algo_bytes,
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth"},
+        "fp64_path": fp64,
+        "speedup_vs_fp64": (value / fp64["solves_per_s"]) if fp64 else None,
+        "solves": infos,
+    }
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        v, dt = cpu_oracle_sample(U, KAPPA)
+        import oracle
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"1 of 12 columns of the 8- and 16-thick slab propagators "
+                                          f"({dt:.1f} s of FP64 CPU work), rate per 12-column solve"}
+    ddp.ddp_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    U = synth.gauge_field(L, seed=synth.SEED_GAUGE)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(U, KAPPA)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_oracle_sample(U, KAPPA)
+    dt = time.perf_counter() - t0
+    value = args.steps * (2.0 / 12.0) / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded SU(3) field, plaquette 0.59)",
+            "config": {"workload": f"48x24^3 nested time slabs 8/16/24 + full lattice, 12-column point-source "
+                                   f"propagators, kappa {KAPPA}, tol {TOL}", "kappa": KAPPA},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": value,
+                             "sample": "per step: 1 of 12 columns of the 8- and 16-thick slab propagators"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16", choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -55,6 +55,8 @@ struct HopArgs {
     FieldView v2;   // second same-parity operand (EPI_RESID: eta)
     FieldView rh;   // shadow residual for DOT_RHAT
     Partials part;
+    const SolveState *st;  // with skip: columns whose solve is not active are left untouched
+    int skip;
 };
 
 // Map a block/thread of a tile-structured launch to (item, column, site).
@@ -129,6 +131,7 @@ __global__ void __launch_bounds__(512) k_hop(HopArgs a) {
     __shared__ Item it;
     load_item(a.L, it);
     TileCoord tc = tile_coord(it, a.L);
+    if (a.skip && tc.valid && !a.st[it.solve0 + tc.col].active) tc.valid = false;
     double cre = 0, cim = 0, nn = 0;
     if (tc.valid) {
         cx<R> acc[4][3];
@@ -215,6 +218,7 @@ struct BlasArgs {
     FieldView x, r, rh, p, v, s, t;
     const SolveState *st;
     Partials part;
+    int skip;
 };
 
 template <class P, int OP>
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
     __shared__ Item it;
     load_item(a.L, it);
     TileCoord tc = tile_coord(it, a.L);
+    if (a.skip && tc.valid && !a.st[it.solve0 + tc.col].active) tc.valid = false;
     double cre = 0, cim = 0, nn = 0;
     if (tc.valid) {
         int64_t i = tc.cb + tc.h;

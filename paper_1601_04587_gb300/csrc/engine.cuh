@@ -46,8 +46,10 @@ struct Engine {
     }
 
     HopArgs hop_args(int par, FieldView in, FieldView out, FieldView v1, FieldView v2, FieldView rhv,
-                     Partials part) {
+                     Partials part, int skip = 0) {
         HopArgs a;
+        a.st = d_st;
+        a.skip = skip;
         a.L = L;
         a.p = par;
         a.in = in;
@@ -66,8 +68,9 @@ struct Engine {
     }
 
     template <class Q, int OP>
-    void blas(Partials part) {
+    void blas(Partials part, int skip = 1) {
         BlasArgs a;
+        a.skip = skip;
         a.L = L;
         a.x = xi;
         a.r = r;
@@ -98,6 +101,7 @@ struct Engine {
     void norm64(FieldView f, Partials part) {
         BlasArgs a;
         memset(&a, 0, sizeof(a));
+        a.skip = 0;
         a.L = L;
         a.x = f;
         a.st = d_st;
@@ -122,12 +126,12 @@ struct Engine {
     // One BiCGStab iteration on the Schur complement (van der Vorst 1992).
     void iteration_body() {
         FieldView none = {nullptr, nullptr, 0};
-        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, p, tmp, none, none, none, A));      // tmp = H_oe p
-        hop<P, EPI_MHAT, DOT_RHAT>(hop_args(0, tmp, v, p, none, rh, A));           // v = p - k^2 H_eo tmp
+        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, p, tmp, none, none, none, A, 1));   // tmp = H_oe p
+        hop<P, EPI_MHAT, DOT_RHAT>(hop_args(0, tmp, v, p, none, rh, A, 1));        // v = p - k^2 H_eo tmp
         fin<FIN_ALPHA>();                                                           // alpha = rho / (rh, v)
         blas<P, OP_S_UPDATE>(A);                                                    // s = r - alpha v
-        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, s, tmp, none, none, none, A));      // tmp = H_oe s
-        hop<P, EPI_MHAT, DOT_TS>(hop_args(0, tmp, t, s, none, none, A));           // t = s - k^2 H_eo tmp
+        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, s, tmp, none, none, none, A, 1));   // tmp = H_oe s
+        hop<P, EPI_MHAT, DOT_TS>(hop_args(0, tmp, t, s, none, none, A, 1));        // t = s - k^2 H_eo tmp
         fin<FIN_OMEGA>();                                                           // omega = (t,s)/(t,t)
         blas<P, OP_XR_UPDATE>(A);                                                   // x, r; (rh,r), (r,r)
         fin<FIN_RHO>();                                                             // beta, convergence
@@ -295,7 +299,7 @@ struct Engine {
             conv(true, s, re64);
             conv(true, ro, ro64);
             hop<P, EPI_AXPY_K, DOT_NORM>(hop_args(0, ro, r, s, none, none, A));  // r = r'_e + k H_eo r'_o
-            blas<P, OP_INIT>(A);
+            blas<P, OP_INIT>(A, 0);
             DDP_CUDA(ctx, cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), st));
             fin<FIN_INIT>();
             DDP_CUDA(ctx, cudaGetLastError());
@@ -381,6 +385,8 @@ int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *ou
     L.CG = plan.CG;
     FieldView none = {nullptr, nullptr, 0};
     HopArgs h;
+    h.st = nullptr;
+    h.skip = 0;
     h.L = L;
     h.v2 = none;
     h.rh = none;
@@ -441,6 +447,8 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, 
     L.CG = plan.CG;
     HopArgs h;
     FieldView none = {nullptr, nullptr, 0};
+    h.st = nullptr;
+    h.skip = 0;
     h.L = L;
     h.p = 0;
     h.in = in;
