@@ -235,6 +235,35 @@ long ddp_kernel_launches(const ddp_ctx *ctx);
 /* Clears the serving state (pending and finished requests). */
 int ddp_serve_reset(ddp_ctx *ctx);
 
+/* ---- allocation-free contraction ------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * must not allocate device memory, for instance code running under another
+ * runtime's memory manager (a framework's custom operator whose allocator
+ * owns the device), code that enqueues work while a CUDA graph is being
+ * captured, or latency-critical loops where cudaMalloc/cudaFree would
+ * synchronise the device.  It computes exactly what ddp_contract computes
+ * (same kernels, same reduction order) without a context and without
+ * allocating: the per-time-slice partial sums go to one fixed device array
+ * of DDP_STATIC_PARTIALS_MAX double2 entries (2 MiB) that lives in the
+ * library and stays held on every GPU that loads it until the process exits.
+ *
+ *  - S, eta (noise kind only) and C_out must be device pointers; C_out gets
+ *    2*L[0] doubles (2 for PSEUDO_LOCAL).  Geometry as in ddp_set_domain.
+ *  - The partial sums need extent[0] * ceil(extent[1]*extent[2]*extent[3] / T)
+ *    entries with T = 32 for NUCLEON and 128 otherwise; more than
+ *    DDP_STATIC_PARTIALS_MAX returns DDP_ERR_INVALID_ARG and launches nothing.
+ *  - The first call on a device looks up the device address of the array
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.  Later calls only enqueue kernels on
+ *    cuda_stream.
+ *  - All calls share the array.  Each call writes every entry it reads, so
+ *    nothing has to be cleared between calls, but calls that may overlap on
+ *    the GPU (different streams without ordering between them) race on it.
+ *  - Returns DDP_OK once the kernels are enqueued; it does not synchronise. */
+#define DDP_STATIC_PARTIALS_MAX (1 << 17)
+int ddp_contract_static(int kind, const int L[4], const int origin[4], const int extent[4], const double *S,
+                        const double *eta, int ncol, const int src[4], double *C_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,7 @@ def lib():
             "ddp_time_hop": ([vp, i, d, i, i, i, ctypes.POINTER(ctypes.c_float),
                               ctypes.POINTER(ctypes.c_double)], i),
             "ddp_kernel_launches": ([vp], ctypes.c_long),
+            "ddp_contract_static": ([i, i4, i4, i4, vp, vp, i, i4, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -281,6 +282,14 @@ def ddp_time_hop(ctx, domain_id, kappa, ncol, precision, iters):
 
 def ddp_kernel_launches(ctx) -> int:
     return int(lib().ddp_kernel_launches(ctx))
+
+
+def ddp_contract_static(kind, L, origin, extent, S, C_out, eta=None, ncol=12, src=(0, 0, 0, 0), stream=None):
+    """Allocation-free contraction for callers that must not allocate device
+    memory (see include/ddp.h); device buffers only, enqueued on `stream`."""
+    s = ctypes.c_void_p(int(stream)) if stream else None
+    return _check(None, lib().ddp_contract_static(int(kind), _i4(L), _i4(origin), _i4(extent), _ptr(S), _ptr(eta),
+                                                  int(ncol), _i4(src), _ptr(C_out), s), "ddp_contract_static")
 
 
 def info_dict(info: ddp_solve_info) -> dict:

@@ -368,3 +368,104 @@ extern "C" int ddp_contract(ddp_ctx *ctx, int kind, int domain_id, const double 
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "contraction");
     return DDP_OK;
 }
+
+// ------------------------------------------------ allocation-free contraction
+//
+// Same kernels as ddp_contract, but the per-time-slice partial sums live in a
+// fixed array in this file instead of memory the library allocates.  Every
+// partial a call reads is first written by the same call, so the array needs
+// no clearing; calls that overlap on the GPU share it and race.
+
+#include <mutex>
+
+#define DDP_STATIC_PARTIALS DDP_STATIC_PARTIALS_MAX
+
+static __device__ __align__(256) double2 g_contract_partials[DDP_STATIC_PARTIALS];
+
+namespace {
+
+std::mutex g_static_mu;
+double2 *g_static_ptr[64] = {nullptr};  // per device: device address of g_contract_partials
+
+}  // namespace
+
+extern "C" int ddp_contract_static(int kind, const int L[4], const int origin[4], const int extent[4],
+                                   const double *S, const double *eta, int ncol, const int src[4], double *C_out,
+                                   void *cuda_stream) {
+    if (!L || !origin || !extent || !S || !C_out) return DDP_ERR_INVALID_ARG;
+    if (kind < 0 || kind > 3) return DDP_ERR_INVALID_ARG;
+    int64_t n = 1;
+    for (int m = 0; m < 4; m++) {
+        if (L[m] < 2 || L[m] % 2 || extent[m] < 1 || extent[m] > L[m]) return DDP_ERR_INVALID_ARG;
+        n *= extent[m];
+    }
+    if (extent[3] % 2) return DDP_ERR_INVALID_ARG;
+    if (kind == DDP_CONTRACT_PSEUDO_NOISE) {
+        if (!eta || ncol < 1) return DDP_ERR_INVALID_ARG;
+    } else if (kind == DDP_CONTRACT_PION) {
+        if (ncol < 1) return DDP_ERR_INVALID_ARG;
+    } else {
+        ncol = 12;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DDP_ERR_CUDA;
+    double2 *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            // host code only holds a stand-in for the device array: fetch its device address once per device
+            double2 *p = nullptr;
+            if (cudaGetSymbolAddress((void **)&p, g_contract_partials) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return DDP_ERR_CUDA;
+            }
+            g_static_ptr[dev] = p;
+        }
+        scratch = g_static_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    Item it;
+    memset(&it, 0, sizeof(it));
+    int par = 0;
+    for (int m = 0; m < 4; m++) {
+        it.o[m] = ((origin[m] % L[m]) + L[m]) % L[m];
+        it.e[m] = extent[m];
+        it.L[m] = L[m];
+        par += it.o[m];
+    }
+    it.par_o = par & 1;
+    it.nh = (int)(n / 2);
+    it.ncol = ncol;
+    if (kind == DDP_CONTRACT_PSEUDO_LOCAL) {
+        if (!src) return DDP_ERR_INVALID_ARG;
+        int k[4];
+        for (int m = 0; m < 4; m++) {
+            if (src[m] < 0 || src[m] >= L[m]) return DDP_ERR_INVALID_ARG;
+            k[m] = ((src[m] - it.o[m]) % L[m] + L[m]) % L[m];
+            if (k[m] >= extent[m]) return DDP_ERR_INVALID_ARG;
+        }
+        int l = ((k[0] * extent[1] + k[1]) * extent[2] + k[2]) * extent[3] + k[3];
+        k_local_trace<<<1, 1, 0, st>>>((const double2 *)S, n, l, (double2 *)C_out);
+        return cudaGetLastError() == cudaSuccess ? DDP_OK : DDP_ERR_CUDA;
+    }
+    int slice_n = extent[1] * extent[2] * extent[3];
+    int threads = (kind == DDP_CONTRACT_NUCLEON) ? 32 : 128;
+    int nchunk = (slice_n + threads - 1) / threads;
+    if ((int64_t)extent[0] * nchunk > DDP_STATIC_PARTIALS) return DDP_ERR_INVALID_ARG;
+    ContractArgs a;
+    a.it = it;
+    a.S = (const double2 *)S;
+    a.eta = (const double2 *)eta;
+    a.ncol = ncol;
+    a.kind = kind;
+    a.nchunk = nchunk;
+    a.part = scratch;
+    size_t smem = (kind == DDP_CONTRACT_NUCLEON) ? threads * 144 * sizeof(Cplx) : 0;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_contract_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return DDP_ERR_CUDA;
+    dim3 grid(nchunk, extent[0]);
+    k_contract_slice<<<grid, threads, smem, st>>>(a);
+    k_contract_final<<<L[0], 256, 0, st>>>(it, scratch, nchunk, (double2 *)C_out);
+    return cudaGetLastError() == cudaSuccess ? DDP_OK : DDP_ERR_CUDA;
+}
