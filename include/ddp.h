@@ -214,8 +214,8 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
 /* Solver knobs: "max_outer" (defect-correction cycles), "max_inner"
  * (BiCGStab iterations per cycle), "delta_fp64" / "delta_fp32" /
  * "delta_fp16" / "delta_bf16" (smallest inner relative tolerance per storage
- * format), "tile_sites" (sites per block, multiple of 32, 0 = automatic),
- * "tile_cols" (columns per block, 0 = automatic), "conditional" (1: the
+ * format), "tile_sites" (sites per block tile: 32; 0 = automatic),
+ * "tile_cols" (columns per block, 1..12, 0 = automatic), "conditional" (1: the
  * inner loop is a device-driven CUDA-graph WHILE node; 0: host-polled graph
  * chunks).  DDP_ERR_INVALID_ARG for unknown names or values. */
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value);

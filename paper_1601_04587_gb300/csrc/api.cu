@@ -49,8 +49,8 @@ Arena::~Arena() {
 void make_plan(const std::vector<Job> &jobs, int prec, const EngineParams &prm, Plan &plan) {
     int maxcol = 1;
     for (auto &j : jobs) maxcol = std::max(maxcol, j.ncol);
-    int CG = prm.CG ? prm.CG : std::min(maxcol, 12);
-    int TS = prm.TS ? prm.TS : 32 * std::max(1, std::min(8, 8 / CG));
+    int CG = std::min(prm.CG ? prm.CG : maxcol, HOP_MAX_CG);
+    int TS = HOP_TS;
     plan.TS = TS;
     plan.CG = CG;
     plan.items.clear();
@@ -841,14 +841,12 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
     else if (n == "delta_fp16") p.floor_delta[2] = value;
     else if (n == "delta_bf16") p.floor_delta[3] = value;
     else if (n == "tile_sites") {
-        if (value != 0 && ((int)value % 32 || value > 512)) return DDP_ERR_INVALID_ARG;
-        p.TS = (int)value;
+        if (value != 0 && value != HOP_TS) return DDP_ERR_INVALID_ARG;
     } else if (n == "tile_cols") {
-        if (value < 0 || value > 16) return DDP_ERR_INVALID_ARG;
+        if (value < 0 || value > HOP_MAX_CG) return DDP_ERR_INVALID_ARG;
         p.CG = (int)value;
     } else if (n == "conditional") p.use_conditional = value != 0;
     else return DDP_ERR_INVALID_ARG;
-    if (p.TS * std::max(p.CG, 1) > 512) return DDP_ERR_INVALID_ARG;
     return DDP_OK;
 }
 

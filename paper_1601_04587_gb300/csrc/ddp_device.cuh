@@ -446,70 +446,14 @@ __device__ __forceinline__ void accumulate(cx<R> acc[4][3], const cx<R> w[2][3],
     }
 }
 
-// One direction, both senses, of the masked hopping term at local site k
-// (global x, parity p).  in: the opposite-parity field, column base cb.
-template <class P, int MU>
-__device__ __forceinline__ void hop_dir(const Item &it, const FieldView &in, int64_t cb, const int k[4],
-                                        const int x[4], int p, cx<typename P::real> acc[4][3]) {
-    using R = typename P::real;
-    const bool restricted = (it.rmask >> MU) & 1;
-    // forward: U_mu(x) psi(x + mu)
-    {
-        int kn[4] = {k[0], k[1], k[2], k[3]};
-        kn[MU] += 1;
-        bool ok = true;
-        if (restricted) {
-            ok = kn[MU] < it.e[MU];
-        } else if (kn[MU] == it.e[MU]) {
-            kn[MU] = 0;
-        }
-        R f = R(1);
-        if (MU == 0 && x[0] == it.L[0] - 1) {
-            if (it.bc == 1) f = R(-1);
-            if (it.bc == 2) ok = false;
-        }
-        if (ok) {
-            R v[24];
-            load_spinor<P>(in, cb + (local_lex(it, kn) >> 1), v);
-            cx<R> h[2][3], w[2][3], u[3][3];
-            project<MU, true>(v, h);
-            load_link<P>(P::IS64 ? it.links64 : it.links, it.gV, MU, link_row(it, x, p), u);
-            su3_mul_half(u, h, w);
-            accumulate<MU, true>(acc, w, f);
-        }
-    }
-    // backward: U_mu(x - mu)^+ psi(x - mu)
-    {
-        int kn[4] = {k[0], k[1], k[2], k[3]};
-        kn[MU] -= 1;
-        bool ok = true;
-        if (restricted) {
-            ok = kn[MU] >= 0;
-        } else if (kn[MU] < 0) {
-            kn[MU] = it.e[MU] - 1;
-        }
-        R f = R(1);
-        if (MU == 0 && x[0] == 0) {
-            if (it.bc == 1) f = R(-1);
-            if (it.bc == 2) ok = false;
-        }
-        if (ok) {
-            R v[24];
-            load_spinor<P>(in, cb + (local_lex(it, kn) >> 1), v);
-            cx<R> h[2][3], w[2][3], u[3][3];
-            project<MU, false>(v, h);
-            int xm[4] = {x[0], x[1], x[2], x[3]};
-            xm[MU] = (xm[MU] == 0) ? it.L[MU] - 1 : xm[MU] - 1;
-            load_link<P>(P::IS64 ? it.links64 : it.links, it.gV, MU, link_row(it, xm, p ^ 1), u);
-            su3_adj_mul_half(u, h, w);
-            accumulate<MU, false>(acc, w, f);
-        }
-    }
-}
-
+// Geometry of one hop d = 2 mu + (backward ? 1 : 0) from even-odd site h of
+// parity p: the neighbour's even-odd index (or -1 when the hop is dropped)
+// and the link the neighbour is transported with, U_mu(x) forward and
+// U_mu(x - mu)^+ backward, multiplied by the boundary factor of the hop
+// (-1 across an antiperiodic time boundary).
 template <class P>
-__device__ __forceinline__ void hop_site(const Item &it, const FieldView &in, int64_t cb, int h, int p,
-                                         cx<typename P::real> acc[4][3]) {
+__device__ __forceinline__ int stage_hop(const Item &it, int h, int p, int d, cx<typename P::real> u[3][3]) {
+    using R = typename P::real;
     int k[4], x[4];
     decode_site(it, h, p, k);
 #pragma unroll
@@ -517,14 +461,59 @@ __device__ __forceinline__ void hop_site(const Item &it, const FieldView &in, in
         int t = it.o[m] + k[m];
         x[m] = (t >= it.L[m]) ? t - it.L[m] : t;
     }
+    const int mu = d >> 1;
+    const bool fwd = !(d & 1);
+    int kn[4] = {k[0], k[1], k[2], k[3]};
+    bool ok = true;
+    const bool restricted = (it.rmask >> mu) & 1;
+    if (fwd) {
+        kn[mu] += 1;
+        if (restricted)
+            ok = kn[mu] < it.e[mu];
+        else if (kn[mu] == it.e[mu])
+            kn[mu] = 0;
+    } else {
+        kn[mu] -= 1;
+        if (restricted)
+            ok = kn[mu] >= 0;
+        else if (kn[mu] < 0)
+            kn[mu] = it.e[mu] - 1;
+    }
+    R f = R(1);
+    if (mu == 0 && x[0] == (fwd ? it.L[0] - 1 : 0)) {
+        if (it.bc == 1) f = R(-1);
+        if (it.bc == 2) ok = false;
+    }
+    if (!ok) return -1;
+    const void *lk = P::IS64 ? it.links64 : it.links;
+    if (fwd) {
+        load_link<P>(lk, it.gV, mu, link_row(it, x, p), u);
 #pragma unroll
-    for (int s = 0; s < 4; s++)
+        for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int a = 0; a < 3; a++) acc[s][a] = mk<typename P::real>(0, 0);
-    hop_dir<P, 0>(it, in, cb, k, x, p, acc);
-    hop_dir<P, 1>(it, in, cb, k, x, p, acc);
-    hop_dir<P, 2>(it, in, cb, k, x, p, acc);
-    hop_dir<P, 3>(it, in, cb, k, x, p, acc);
+            for (int j = 0; j < 3; j++) u[i][j] = f * u[i][j];
+    } else {
+        int xm[4] = {x[0], x[1], x[2], x[3]};
+        xm[mu] = (xm[mu] == 0) ? it.L[mu] - 1 : xm[mu] - 1;
+        cx<R> v[3][3];
+        load_link<P>(lk, it.gV, mu, link_row(it, xm, p ^ 1), v);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) u[i][j] = f * conj(v[j][i]);
+    }
+    return local_lex(it, kn) >> 1;
+}
+
+// acc += (1 -/+ g_mu) u psi for hop D (compile-time), link u already oriented.
+template <int D, typename R>
+__device__ __forceinline__ void hop_step(const R v[24], const cx<R> u[3][3], cx<R> acc[4][3]) {
+    constexpr int MU = D >> 1;
+    constexpr bool FWD = !(D & 1);
+    cx<R> h[2][3], w[2][3];
+    project<MU, FWD>(v, h);
+    su3_mul_half(u, h, w);
+    accumulate<MU, FWD>(acc, w, R(1));
 }
 
 // --------------------------------------------------------- reductions

@@ -125,17 +125,73 @@ __device__ __forceinline__ void load_item(const Launch &L, Item &dst) {
 
 // ------------------------------------------------------------ hopping kernel
 
+// Tiles of TS sites: the links (oriented, boundary sign folded in, row 2
+// rebuilt) and neighbour indices of the tile's 8 TS hops are staged in shared
+// memory once and shared by the CG column-threads of every site.
+// Tiles are exactly HOP_TS = 32 sites (one warp per column of a tile); a
+// block holds at most HOP_MAX_CG = 12 columns.
+constexpr int HOP_TS = 32;
+constexpr int HOP_MAX_CG = 12;
+
 template <class P, int EPI, int DOT>
-__global__ void __launch_bounds__(512) k_hop(HopArgs a) {
+__global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 2) k_hop(HopArgs a) {
     using R = typename P::real;
+    constexpr int TSMAX = HOP_TS;
     __shared__ Item it;
+    __shared__ int s_nb[8 * TSMAX];
+    __shared__ R s_u[18][8 * TSMAX];
     load_item(a.L, it);
+    const int TS = a.L.TS;
+    {
+        const int tile = (blockIdx.x - it.blk0) % it.ntiles;
+        for (int q = threadIdx.x; q < 8 * TS; q += blockDim.x) {
+            const int d = q / TS, sidx = q - d * TS, h = tile * TS + sidx;
+            int nb = -1;
+            cx<R> u[3][3];
+            if (h < it.nh) nb = stage_hop<P>(it, h, a.p, d, u);
+            s_nb[q] = nb;
+            if (nb >= 0) {
+#pragma unroll
+                for (int k = 0; k < 9; k++) {
+                    s_u[2 * k][q] = u[k / 3][k % 3].re;
+                    s_u[2 * k + 1][q] = u[k / 3][k % 3].im;
+                }
+            }
+        }
+    }
+    __syncthreads();
     TileCoord tc = tile_coord(it, a.L);
     if (a.skip && tc.valid && !a.st[it.solve0 + tc.col].active) tc.valid = false;
     double cre = 0, cim = 0, nn = 0;
     if (tc.valid) {
         cx<R> acc[4][3];
-        hop_site<P>(it, a.in, tc.cb, tc.h, a.p, acc);
+#pragma unroll
+        for (int s2 = 0; s2 < 4; s2++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc[s2][c] = mk<R>(0, 0);
+        const int sl = tc.h - tc.tile * TS;
+#define DDP_HOP_STEP(D)                                                   \
+        {                                                                 \
+            const int q = (D) * TS + sl;                                  \
+            const int nb = s_nb[q];                                       \
+            if (nb >= 0) {                                                \
+                R v[24];                                                  \
+                load_spinor<P>(a.in, tc.cb + nb, v);                      \
+                cx<R> u[3][3];                                            \
+                _Pragma("unroll") for (int k = 0; k < 9; k++)             \
+                    u[k / 3][k % 3] = mk(s_u[2 * k][q], s_u[2 * k + 1][q]); \
+                hop_step<D>(v, u, acc);                                   \
+            }                                                             \
+        }
+        DDP_HOP_STEP(0)
+        DDP_HOP_STEP(1)
+        DDP_HOP_STEP(2)
+        DDP_HOP_STEP(3)
+        DDP_HOP_STEP(4)
+        DDP_HOP_STEP(5)
+        DDP_HOP_STEP(6)
+        DDP_HOP_STEP(7)
+#undef DDP_HOP_STEP
         R o[24];
         int64_t i = tc.cb + tc.h;
         const R kap = (R)it.kappa;
