@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ddp.h"
+#include "ddp.h"
 #include "ddp_kernels.cuh"
 
 namespace ddp {
