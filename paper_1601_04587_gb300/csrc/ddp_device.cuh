@@ -518,7 +518,8 @@ __device__ __forceinline__ void hop_step(const R v[24], const cx<R> u[3][3], cx<
 
 // --------------------------------------------------------- reductions
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;

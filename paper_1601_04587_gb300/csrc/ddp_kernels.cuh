@@ -80,11 +80,16 @@ __device__ __forceinline__ TileCoord tile_coord(const Item &it, const Launch &L)
     return t;
 }
 
-// Block reduction of (complex, real) per column: lanes of a warp share one
-// column (TS is a multiple of 32); warps of the same column are added in
-// warp order.  Fixed order: results do not depend on the batch around them.
-__device__ __forceinline__ void block_partials(const Item &it, const Launch &L, const TileCoord &tc, double cre,
-                                               double cim, double nn, Partials part, bool want_c, bool want_n) {
+// Block reduction of (complex, real) per column.  Each thread's products and
+// the 32-lane warp sums are formed in the compute precision R (FP32 for the
+// low-precision formats: FP64 arithmetic is a small fraction of GB300's FP32
+// rate); the sums across warps and, in the scalar kernels, across blocks are
+// FP64.  Lanes of a warp share one column (TS = 32); warps of the same
+// column are added in warp order.  Fixed order: results do not depend on
+// the batch around them.
+template <typename R>
+__device__ __forceinline__ void block_partials(const Item &it, const Launch &L, const TileCoord &tc, R cre, R cim,
+                                               R nn, Partials part, bool want_c, bool want_n) {
     __shared__ double s_re[32], s_im[32], s_nn[32];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (want_c) {
@@ -93,9 +98,9 @@ __device__ __forceinline__ void block_partials(const Item &it, const Launch &L, 
     }
     if (want_n) nn = warp_sum(nn);
     if (lane == 0) {
-        s_re[warp] = cre;
-        s_im[warp] = cim;
-        s_nn[warp] = nn;
+        s_re[warp] = (double)cre;
+        s_im[warp] = (double)cim;
+        s_nn[warp] = (double)nn;
     }
     __syncthreads();
     int wpc = L.TS >> 5;  // warps per column
@@ -134,7 +139,7 @@ constexpr int HOP_TS = 32;
 constexpr int HOP_MAX_CG = 12;
 
 template <class P, int EPI, int DOT>
-__global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 2) k_hop(HopArgs a) {
+__global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_hop(HopArgs a) {
     using R = typename P::real;
     constexpr int TSMAX = HOP_TS;
     __shared__ Item it;
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 2) k_
     __syncthreads();
     TileCoord tc = tile_coord(it, a.L);
     if (a.skip && tc.valid && !a.st[it.solve0 + tc.col].active) tc.valid = false;
-    double cre = 0, cim = 0, nn = 0;
+    R cre = 0, cim = 0, nn = 0;
     if (tc.valid) {
         cx<R> acc[4][3];
 #pragma unroll
@@ -239,8 +244,8 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 2) k_
                 load_spinor<P>(a.v1, i, s1);
 #pragma unroll
                 for (int j = 0; j < 12; j++) {
-                    cre += (double)(o[2 * j] * s1[2 * j] + o[2 * j + 1] * s1[2 * j + 1]);
-                    cim += (double)(o[2 * j] * s1[2 * j + 1] - o[2 * j + 1] * s1[2 * j]);
+                    cre += o[2 * j] * s1[2 * j] + o[2 * j + 1] * s1[2 * j + 1];
+                    cim += o[2 * j] * s1[2 * j + 1] - o[2 * j + 1] * s1[2 * j];
                 }
             }
         }
@@ -250,14 +255,14 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 2) k_
             load_spinor<P>(a.rh, i, r);
 #pragma unroll
             for (int j = 0; j < 12; j++) {
-                cre += (double)(r[2 * j] * o[2 * j] + r[2 * j + 1] * o[2 * j + 1]);
-                cim += (double)(r[2 * j] * o[2 * j + 1] - r[2 * j + 1] * o[2 * j]);
+                cre += r[2 * j] * o[2 * j] + r[2 * j + 1] * o[2 * j + 1];
+                cim += r[2 * j] * o[2 * j + 1] - r[2 * j + 1] * o[2 * j];
             }
         }
         if (DOT == DOT_TS || DOT == DOT_NORM) {
-            double s = 0;
+            R s = 0;
 #pragma unroll
-            for (int j = 0; j < 24; j++) s += (double)(o[j] * o[j]);
+            for (int j = 0; j < 24; j++) s += o[j] * o[j];
             nn = s;
         }
     }
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
     load_item(a.L, it);
     TileCoord tc = tile_coord(it, a.L);
     if (a.skip && tc.valid && !a.st[it.solve0 + tc.col].active) tc.valid = false;
-    double cre = 0, cim = 0, nn = 0;
+    R cre = 0, cim = 0, nn = 0;
     if (tc.valid) {
         int64_t i = tc.cb + tc.h;
         const SolveState &S = a.st[it.solve0 + tc.col];
@@ -331,12 +336,12 @@ __global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
             store_spinor<P>(a.r, i, s);
             R rh[24];
             load_spinor<P>(a.rh, i, rh);
-            double n2 = 0;
+            R n2 = 0;
 #pragma unroll
             for (int j = 0; j < 12; j++) {
-                cre += (double)(rh[2 * j] * s[2 * j] + rh[2 * j + 1] * s[2 * j + 1]);
-                cim += (double)(rh[2 * j] * s[2 * j + 1] - rh[2 * j + 1] * s[2 * j]);
-                n2 += (double)(s[2 * j] * s[2 * j] + s[2 * j + 1] * s[2 * j + 1]);
+                cre += rh[2 * j] * s[2 * j] + rh[2 * j + 1] * s[2 * j + 1];
+                cim += rh[2 * j] * s[2 * j + 1] - rh[2 * j + 1] * s[2 * j];
+                n2 += s[2 * j] * s[2 * j] + s[2 * j + 1] * s[2 * j + 1];
             }
             nn = n2;
         } else if (OP == OP_INIT) {  // rh = r ; p = r ; x = 0
@@ -350,9 +355,9 @@ __global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
         } else if (OP == OP_NORM) {  // |x|^2
             R x[24];
             load_spinor<P>(a.x, i, x);
-            double n2 = 0;
+            R n2 = 0;
 #pragma unroll
-            for (int j = 0; j < 24; j++) n2 += (double)(x[j] * x[j]);
+            for (int j = 0; j < 24; j++) n2 += x[j] * x[j];
             nn = n2;
         }
     }
