@@ -284,9 +284,12 @@ struct Engine {
         int cycles = 0;
         bool all_done = false;
         for (int cyc = 0; cyc <= prm.max_outer; cyc++) {
-            // r64 = eta - D_Gamma x  (FP64 links, FP64 vectors)
-            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A));
-            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B));
+            // r64 = eta - D_Gamma x  (FP64 links, FP64 vectors).  At the first
+            // cycle x = 0, so r64 = eta and the partials of |eta|^2 are reused.
+            if (cyc > 0) {
+                hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A));
+                hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B));
+            }
             fin<FIN_RESID>();
             DDP_CUDA(ctx, cudaMemcpyAsync(h_st.data(), d_st, plan.nsolve * sizeof(SolveState),
                                           cudaMemcpyDeviceToHost, st));
@@ -296,8 +299,8 @@ struct Engine {
             if (all_done || cyc == prm.max_outer) break;
             cycles++;
             // normalised defect in storage format, even-odd right-hand side
-            conv(true, s, re64);
-            conv(true, ro, ro64);
+            conv(true, s, cyc ? re64 : be);
+            conv(true, ro, cyc ? ro64 : bo);
             hop<P, EPI_AXPY_K, DOT_NORM>(hop_args(0, ro, r, s, none, none, A));  // r = r'_e + k H_eo r'_o
             blas<P, OP_INIT>(A, 0);
             DDP_CUDA(ctx, cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), st));
