@@ -191,22 +191,43 @@ int ddp_series_terms(ddp_ctx *ctx, int domain_small, const double *S_small, int 
 int ddp_contract(ddp_ctx *ctx, int kind, int domain_id, const double *S, const double *eta, int ncol,
                  const int src[4], double *C_out);
 
-/* ---- serving: continuous batching of propagator solves ------------------
- * Requests are admitted while the context's memory budget and slot count
- * allow; admitted requests join the running device loop at its next
- * admission point, so work of requests that arrive while others run
- * overlaps on the GPU.  Each result equals the result of the same request
- * solved alone (deterministic per-request reductions). */
+/* Level-1 averaging of the two-level integration (Sec. 3, Eq. factsing): with
+ * T_A[v][L0] and T_B[w][L0] the time-slice traces (complex) of region A for
+ * nvar_A level-1 variants and of region B for nvar_B variants,
+ *   C_out[y0][x0] = (1/L^3) * mean_v T_A^v(x0) * mean_w T_B^w(y0)
+ * (complex, L0 x L0).  spatial_volume = L^3.  Buffers host or device. */
+int ddp_factorized_correlator(ddp_ctx *ctx, const double *T_A, int nvar_A, const double *T_B, int nvar_B, int L0,
+                              double spatial_volume, double *C_out);
 
-/* Configure serving: memory budget in bytes for solver state (0 = 80% of
- * free device memory) and the maximum number of concurrently active requests. */
+/* ---- serving: continuous batching of propagator solves ------------------
+ * A server owns a fixed-capacity set of resident solver fields sized by its
+ * memory budget.  ddp_submit admits a request at once if an active slot and
+ * enough contiguous capacity are free, and returns DDP_ERR_BUSY otherwise
+ * (retry after a ddp_serve_step has retired work).  Each ddp_serve_step runs
+ * one defect-correction cycle (FP64 residual, inner BiCGStab loop, FP64
+ * accumulation) for every active request in one launch sequence, so requests
+ * admitted while others are running join them on the device; converged
+ * requests are written to their output buffers and retire.  A request's
+ * result equals the same request solved alone by ddp_solve_propagator /
+ * ddp_solve_sources (bit for bit: per-request fixed-order reductions and
+ * stopping criteria).  Gauge fields and domains must stay loaded while their
+ * requests are in flight. */
+
+/* Configure (or reconfigure, dropping all requests) the server: memory budget
+ * in bytes for its resident fields (0 = 80% of free device memory), the
+ * maximum number of active requests and the storage format of the solves.
+ * DDP_ERR_OOM if the budget cannot hold a useful capacity. */
 int ddp_serve_config(ddp_ctx *ctx, uint64_t mem_budget_bytes, int max_active, int precision);
-/* Submit a request; DDP_ERR_BUSY if it does not fit now.  ticket receives an id. */
+/* Admit a request (eta and out must be device memory; at most 16 columns).
+ * DDP_ERR_BUSY: no slot or capacity free now; DDP_ERR_OOM: larger than the
+ * server's whole capacity.  ticket receives an id on DDP_OK. */
 int ddp_submit(ddp_ctx *ctx, const ddp_solve_req *req, uint64_t *ticket);
-/* Advance the serving loop by one step (admit, iterate, retire). Non-blocking
- * beyond the step itself; returns the number of requests still in flight in *in_flight. */
+/* Run one cycle for all active requests (blocking until it is done);
+ * *in_flight receives the number of requests still active. */
 int ddp_serve_step(ddp_ctx *ctx, int *in_flight);
-/* done = 1 when the request finished (its out buffer is then complete). */
+/* done = 1 when the request has retired; its output buffer is then complete
+ * and info holds its residuals and latency (seconds from submit to retire).
+ * A finished ticket is forgotten after it has been polled once. */
 int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
 
 /* ---- tuning and measurement ---------------------------------------------- */

@@ -55,6 +55,8 @@ def lib():
         L.orc_contract_pion.argtypes = [i4, i4, i4, dp, dp]
         L.orc_contract_nucleon.argtypes = [i4, i4, i4, dp, dp]
         L.orc_contract_noise_trace.argtypes = [i4, i4, i4, dp, dp, ctypes.c_int, dp]
+        L.orc_factorized_correlator.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                dp]
         _lib = L
     return _lib
 
@@ -195,3 +197,13 @@ def noise_trace(L, origin, extent, eta, psi):
     lib().orc_contract_noise_trace(_i4(L), _i4(origin), _i4(extent), _ptr(eta), _ptr(psi), eta.shape[0],
                                    _ptr(out))
     return out[0::2] + 1j * out[1::2]
+
+
+def factorized_correlator(TA, TB, L0, vol3):
+    """C[y0][x0] = (1/L^3) mean_v TA[v][x0] * mean_w TB[w][y0] (Eq. factsing)."""
+    TA = _c(TA)
+    TB = _c(TB)
+    C = np.zeros((L0, L0), dtype=np.complex128)
+    if lib().orc_factorized_correlator(_ptr(TA), TA.shape[0], _ptr(TB), TB.shape[0], int(L0), float(vol3), _ptr(C)):
+        raise ValueError("bad arguments")
+    return C

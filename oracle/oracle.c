@@ -610,3 +610,22 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Two-level factorized correlator (Sec. 3, Eq. factsing): the level-1 means of
+ * the two regions' time-slice traces, multiplied and divided by L^3:
+ *   C[y0][x0] = (1/L^3) (1/nA sum_v TA[v][x0]) (1/nB sum_w TB[w][y0]).
+ * TA [nA][L0], TB [nB][L0], C [L0][L0], all complex. */
+int orc_factorized_correlator(const double *TAd, int nA, const double *TBd, int nB, int L0, double vol3,
+                              double *Cd) {
+    if (nA < 1 || nB < 1 || L0 < 1 || !(vol3 > 0)) return 1;
+    const cplx *TA = (const cplx *)TAd, *TB = (const cplx *)TBd;
+    cplx *C = (cplx *)Cd;
+    for (int y0 = 0; y0 < L0; y0++)
+        for (int x0 = 0; x0 < L0; x0++) {
+            cplx a = 0, b = 0;
+            for (int v = 0; v < nA; v++) a += TA[(int64_t)v * L0 + x0];
+            for (int w = 0; w < nB; w++) b += TB[(int64_t)w * L0 + y0];
+            C[(int64_t)y0 * L0 + x0] = (a / nA) * (b / nB) / vol3;
+        }
+    return 0;
+}

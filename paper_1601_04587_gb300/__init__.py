@@ -89,6 +89,7 @@ def lib():
                               ctypes.POINTER(ctypes.c_double)], i),
             "ddp_kernel_launches": ([vp], ctypes.c_long),
             "ddp_contract_static": ([i, i4, i4, i4, vp, vp, i, i4, vp, vp], i),
+            "ddp_factorized_correlator": ([vp, vp, i, vp, i, i, d, vp], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -237,6 +238,12 @@ def ddp_series_terms(ctx, domain_small, S_small, domain_big, S_big, T_out, ncol=
 def ddp_contract(ctx, kind, domain_id, S, C_out, eta=None, ncol=12, src=(0, 0, 0, 0)):
     return _check(ctx, lib().ddp_contract(ctx, int(kind), int(domain_id), _ptr(S), _ptr(eta), int(ncol), _i4(src),
                                           _ptr(C_out)), "ddp_contract")
+
+
+def ddp_factorized_correlator(ctx, T_A, nvar_A, T_B, nvar_B, L0, spatial_volume, C_out):
+    return _check(ctx, lib().ddp_factorized_correlator(ctx, _ptr(T_A), int(nvar_A), _ptr(T_B), int(nvar_B), int(L0),
+                                                       float(spatial_volume), _ptr(C_out)),
+                  "ddp_factorized_correlator")
 
 
 def ddp_serve_config(ctx, mem_budget_bytes=0, max_active=64, precision=DDP_PREC_MIXED_FP32):

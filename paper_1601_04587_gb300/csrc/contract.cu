@@ -469,3 +469,76 @@ extern "C" int ddp_contract_static(int kind, const int L[4], const int origin[4]
     k_contract_final<<<L[0], 256, 0, st>>>(it, scratch, nchunk, (double2 *)C_out);
     return cudaGetLastError() == cudaSuccess ? DDP_OK : DDP_ERR_CUDA;
 }
+
+// ------------------------------------------- two-level factorized correlator
+//
+// Sec. 3 / Sec. 5 (Eq. factsing): with the spatial links at the cut frozen, the
+// factorized part of the disconnected correlator is the product of the two
+// regions' level-1 averages of the time-slice traces,
+//   C^(f)(y0, x0) = (1/L^3) [mean_v T_A^v(x0)] [mean_w T_B^w(y0)].
+// One thread per (y0, x0); the means are summed in variant order (FP64).
+
+namespace ddp {
+
+__global__ void k_factorized(const double2 *TA, int nA, const double2 *TB, int nB, int L0, double inv_vol,
+                             double2 *C) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= L0 * L0) return;
+    int y0 = g / L0, x0 = g - y0 * L0;
+    double ar = 0, ai = 0, br = 0, bi = 0;
+    for (int v = 0; v < nA; v++) {
+        double2 t = TA[(int64_t)v * L0 + x0];
+        ar += t.x;
+        ai += t.y;
+    }
+    for (int v = 0; v < nB; v++) {
+        double2 t = TB[(int64_t)v * L0 + y0];
+        br += t.x;
+        bi += t.y;
+    }
+    ar /= nA;
+    ai /= nA;
+    br /= nB;
+    bi /= nB;
+    C[g] = make_double2(inv_vol * (ar * br - ai * bi), inv_vol * (ar * bi + ai * br));
+}
+
+}  // namespace ddp
+
+extern "C" int ddp_factorized_correlator(ddp_ctx *ctx, const double *T_A, int nvar_A, const double *T_B, int nvar_B,
+                                         int L0, double spatial_volume, double *C_out) {
+    if (!ctx || !T_A || !T_B || !C_out || nvar_A < 1 || nvar_B < 1 || L0 < 1 || !(spatial_volume > 0))
+        return DDP_ERR_INVALID_ARG;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    cudaStream_t st = ctx->stream;
+    StreamJoin sj(ctx);
+    size_t ba = (size_t)nvar_A * L0 * sizeof(double2), bb = (size_t)nvar_B * L0 * sizeof(double2);
+    size_t bc = (size_t)L0 * L0 * sizeof(double2);
+    void *dA = const_cast<double *>(T_A), *dB = const_cast<double *>(T_B), *dC = C_out;
+    bool oA = !dev_ptr(T_A), oB = !dev_ptr(T_B), oC = !dev_ptr(C_out);
+    cudaError_t e = cudaSuccess;
+    do {
+        if (oA && ((e = cudaMallocAsync(&dA, ba, st)) != cudaSuccess ||
+                   (e = cudaMemcpyAsync(dA, T_A, ba, cudaMemcpyHostToDevice, st)) != cudaSuccess))
+            break;
+        if (oB && ((e = cudaMallocAsync(&dB, bb, st)) != cudaSuccess ||
+                   (e = cudaMemcpyAsync(dB, T_B, bb, cudaMemcpyHostToDevice, st)) != cudaSuccess))
+            break;
+        if (oC && (e = cudaMallocAsync(&dC, bc, st)) != cudaSuccess) break;
+        int n = L0 * L0;
+        k_factorized<<<(n + 255) / 256, 256, 0, st>>>((const double2 *)dA, nvar_A, (const double2 *)dB, nvar_B, L0,
+                                                    1.0 / spatial_volume, (double2 *)dC);
+        ctx->launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if (oC && (e = cudaMemcpyAsync(C_out, dC, bc, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    if (oA && dA) cudaFreeAsync(dA, st);
+    if (oB && dB) cudaFreeAsync(dB, st);
+    if (oC && dC) cudaFreeAsync(dC, st);
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "factorized correlator");
+    return DDP_OK;
+}

@@ -141,6 +141,18 @@ int solve_jobs(ddp_ctx *ctx, int prec, std::vector<Job> &jobs, std::vector<JobIn
 
 int solve_jobs_dispatch(ddp_ctx *ctx, int prec, std::vector<Job> &jobs, std::vector<JobInfo> &infos);
 
+// Continuous-batching server (one per context); see serve_engine.cuh.
+struct ServerBase {
+    int prec = 0;
+    virtual ~ServerBase() {}
+    virtual int submit(const Job &job, uint64_t ticket) = 0;
+    virtual int step(int *in_flight) = 0;
+    virtual int poll(uint64_t ticket, int *done, ddp_solve_info *info) = 0;
+};
+
+template <class P>
+ServerBase *make_server(ddp_ctx *ctx, int prec, uint64_t budget, int max_active, int *status);
+
 // Build the work table of a list of boxes (shared by the engine and apply).
 struct Plan {
     std::vector<Item> items;

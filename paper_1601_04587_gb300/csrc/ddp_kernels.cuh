@@ -569,6 +569,7 @@ struct PackArgs {
     const double2 *user;  // eta (pack) or NULL for a point source
     double2 *uout;        // unpack target
     FieldView fe, fo;     // FP64 even / odd fields
+    FieldView xe, xo;     // pack: solution fields zeroed at the same sites (p == NULL: untouched)
     int src_l;            // point source local index (pack with user == NULL)
 };
 
@@ -606,6 +607,11 @@ static __global__ void k_pack(PackArgs a) {
         if (l == a.src_l) v[2 * col] = 1.0;  // column c = 3 spin + colour is component c
     }
     store_spinor<PF64>(par ? a.fo : a.fe, i, v);
+    if (a.xe.p) {
+#pragma unroll
+        for (int j = 0; j < 24; j++) v[j] = 0.0;
+        store_spinor<PF64>(par ? a.xo : a.xe, i, v);
+    }
 }
 
 static __global__ void k_unpack(PackArgs a) {

@@ -197,135 +197,183 @@ struct Engine {
         return DDP_OK;
     }
 
-    int run(std::vector<Job> &jobs, std::vector<JobInfo> &infos) {
-        const EngineParams &prm = ctx->prm;
-        make_plan(jobs, prec, prm, plan);
-        const int64_t NF = plan.nfield;
-        size_t need = 6 * field_bytes<PF64>(NF) + 9 * field_bytes<P>(NF) +
-                      2 * ((size_t)plan.npart * (sizeof(double2) + sizeof(double)) + 1024) +
-                      plan.items.size() * sizeof(Item) + plan.nsolve * sizeof(SolveState) + sizeof(LoopCtl) + 4096;
-        DDP_CUDA(ctx, ctx->ws.reserve(need));
-        Arena &a = ctx->ws;
+    // ----------------------------------------------------------- building blocks
+
+    static size_t bytes_needed(int64_t cap, int64_t npart, int nitems, int nsolve) {
+        return 6 * field_bytes<PF64>(cap) + 9 * field_bytes<P>(cap) +
+               2 * ((size_t)npart * (sizeof(double2) + sizeof(double)) + 1024) + (size_t)nitems * sizeof(Item) +
+               (size_t)nsolve * sizeof(SolveState) + sizeof(LoopCtl) + 8192;
+    }
+
+    // Every field gets room for cap site-columns per parity (stride cap).
+    void carve(Arena &a, int64_t cap, int64_t npart, int nitems, int nsolve) {
         a.reset();
-        be = carve_field<PF64>(a, NF);
-        bo = carve_field<PF64>(a, NF);
-        xe = carve_field<PF64>(a, NF);
-        xo = carve_field<PF64>(a, NF);
-        re64 = carve_field<PF64>(a, NF);
-        ro64 = carve_field<PF64>(a, NF);
-        r = carve_field<P>(a, NF);
-        rh = carve_field<P>(a, NF);
-        p = carve_field<P>(a, NF);
-        v = carve_field<P>(a, NF);
-        s = carve_field<P>(a, NF);
-        t = carve_field<P>(a, NF);
-        xi = carve_field<P>(a, NF);
-        tmp = carve_field<P>(a, NF);
-        ro = carve_field<P>(a, NF);
-        A.c = (double2 *)a.take(plan.npart * sizeof(double2));
-        A.n = (double *)a.take(plan.npart * sizeof(double));
-        B.c = (double2 *)a.take(plan.npart * sizeof(double2));
-        B.n = (double *)a.take(plan.npart * sizeof(double));
-        d_items = (Item *)a.take(plan.items.size() * sizeof(Item));
-        d_st = (SolveState *)a.take(plan.nsolve * sizeof(SolveState));
+        be = carve_field<PF64>(a, cap);
+        bo = carve_field<PF64>(a, cap);
+        xe = carve_field<PF64>(a, cap);
+        xo = carve_field<PF64>(a, cap);
+        re64 = carve_field<PF64>(a, cap);
+        ro64 = carve_field<PF64>(a, cap);
+        r = carve_field<P>(a, cap);
+        rh = carve_field<P>(a, cap);
+        p = carve_field<P>(a, cap);
+        v = carve_field<P>(a, cap);
+        s = carve_field<P>(a, cap);
+        t = carve_field<P>(a, cap);
+        xi = carve_field<P>(a, cap);
+        tmp = carve_field<P>(a, cap);
+        ro = carve_field<P>(a, cap);
+        A.c = (double2 *)a.take(npart * sizeof(double2));
+        A.n = (double *)a.take(npart * sizeof(double));
+        B.c = (double2 *)a.take(npart * sizeof(double2));
+        B.n = (double *)a.take(npart * sizeof(double));
+        d_items = (Item *)a.take(nitems * sizeof(Item));
+        d_st = (SolveState *)a.take(nsolve * sizeof(SolveState));
         d_ctl = (LoopCtl *)a.take(sizeof(LoopCtl));
+    }
+
+    // Upload the work table of the current plan and the per-column states.
+    int upload(const std::vector<SolveState> &states) {
         cudaStream_t st = ctx->stream;
         L.items = d_items;
         L.nitems = (int)plan.items.size();
         L.TS = plan.TS;
         L.CG = plan.CG;
         threads = plan.TS * plan.CG;
-
-        h_st.assign(plan.nsolve, SolveState());
-        for (size_t i = 0; i < plan.items.size(); i++) {
-            const Item &it = plan.items[i];
-            for (int c = 0; c < it.ncol; c++) {
-                SolveState &S = h_st[it.solve0 + c];
-                memset(&S, 0, sizeof(S));
-                S.item = (int)i;
-                S.col = c;
-                S.tol = jobs[i].tol;
-                S.floor_delta = prm.floor_delta[prec];
-                S.maxit = prm.max_inner;
-                S.status = 4;
-            }
-        }
+        h_st = states;
         DDP_CUDA(ctx, cudaMemcpyAsync(d_items, plan.items.data(), plan.items.size() * sizeof(Item),
                                       cudaMemcpyHostToDevice, st));
         DDP_CUDA(ctx, cudaMemcpyAsync(d_st, h_st.data(), plan.nsolve * sizeof(SolveState), cudaMemcpyHostToDevice,
                                       st));
-        LoopCtl c0 = {0, 0, prm.max_inner, 0};
+        LoopCtl c0 = {0, 0, ctx->prm.max_inner, 0};
         DDP_CUDA(ctx, cudaMemcpyAsync(d_ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+        return DDP_OK;
+    }
 
-        // sources and |eta|^2
-        for (size_t i = 0; i < jobs.size(); i++) {
-            PackArgs pa;
-            memset(&pa, 0, sizeof(pa));
-            pa.it = plan.items[i];
-            pa.user = (const double2 *)jobs[i].eta;
-            pa.fe = be;
-            pa.fo = bo;
-            pa.src_l = jobs[i].src_l;
-            int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
-            k_pack<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(pa);
-            launches++;
-        }
+    SolveState fresh_state(int item, int col, double tol) const {
+        SolveState S;
+        memset(&S, 0, sizeof(S));
+        S.item = item;
+        S.col = col;
+        S.tol = tol;
+        S.floor_delta = ctx->prm.floor_delta[prec];
+        S.maxit = ctx->prm.max_inner;
+        S.status = 4;
+        return S;
+    }
+
+    // eta (or the point sources) of item i into the FP64 source fields; x = 0 there.
+    int pack_source(int i, const Job &job) {
+        cudaStream_t st = ctx->stream;
+        PackArgs pa;
+        memset(&pa, 0, sizeof(pa));
+        pa.it = plan.items[i];
+        pa.user = (const double2 *)job.eta;
+        pa.fe = be;
+        pa.fo = bo;
+        pa.src_l = job.src_l;
+        pa.xe = xe;
+        pa.xo = xo;
+        int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
+        k_pack<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(pa);
+        launches++;
+        return DDP_OK;
+    }
+
+    int unpack_result(int i, double *out) {
+        PackArgs pa;
+        memset(&pa, 0, sizeof(pa));
+        pa.it = plan.items[i];
+        pa.uout = (double2 *)out;
+        pa.fe = xe;
+        pa.fo = xo;
+        int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
+        k_unpack<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(pa);
+        launches++;
+        DDP_CUDA(ctx, cudaGetLastError());
+        return DDP_OK;
+    }
+
+    void source_norms() {
         norm64(be, A);
         norm64(bo, B);
         fin<FIN_BNORM>();
-        DDP_CUDA(ctx, cudaMemsetAsync(xe.p, 0, (size_t)NF * sizeof(double2) * 12, st));
-        DDP_CUDA(ctx, cudaMemsetAsync(xo.p, 0, (size_t)NF * sizeof(double2) * 12, st));
-        DDP_CUDA(ctx, cudaGetLastError());
+    }
 
-        int rc = build_loop_graph();
-        if (rc) return rc;
-
+    // r64 = eta - D_Gamma x (FP64 links and vectors); skip_hop: x is known to be 0,
+    // so r64 = eta and the partials of |eta|^2 left by source_norms() are reused.
+    void residual(bool skip_hop) {
         FieldView none = {nullptr, nullptr, 0};
+        if (!skip_hop) {
+            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A));
+            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B));
+        }
+        fin<FIN_RESID>();
+    }
+
+    int download_states() {
+        DDP_CUDA(ctx, cudaMemcpyAsync(h_st.data(), d_st, plan.nsolve * sizeof(SolveState), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return DDP_OK;
+    }
+
+    // One correction: inner solve of the normalised defect and FP64 accumulation.
+    int correction(bool r_is_eta) {
+        FieldView none = {nullptr, nullptr, 0};
+        conv(true, s, r_is_eta ? be : re64);
+        conv(true, ro, r_is_eta ? bo : ro64);
+        hop<P, EPI_AXPY_K, DOT_NORM>(hop_args(0, ro, r, s, none, none, A));  // r = r'_e + k H_eo r'_o
+        blas<P, OP_INIT>(A, 0);
+        DDP_CUDA(ctx, cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), ctx->stream));
+        fin<FIN_INIT>();
+        DDP_CUDA(ctx, cudaGetLastError());
+        int rc = run_inner();
+        if (rc) return rc;
+        hop<P, EPI_AXPY_K, DOT_NONE>(hop_args(1, xi, tmp, ro, none, none, A));  // e'_o = r'_o + k H_oe e'_e
+        conv(false, xi, xe);
+        conv(false, tmp, xo);
+        return DDP_OK;
+    }
+
+    void drop_graph() {
+        if (loop_exec) cudaGraphExecDestroy(loop_exec);
+        if (loop_graph) cudaGraphDestroy(loop_graph);
+        loop_exec = nullptr;
+        loop_graph = nullptr;
+    }
+
+    // ----------------------------------------------------------- one-shot solve
+
+    int run(std::vector<Job> &jobs, std::vector<JobInfo> &infos) {
+        const EngineParams &prm = ctx->prm;
+        make_plan(jobs, prec, prm, plan);
+        DDP_CUDA(ctx, ctx->ws.reserve(bytes_needed(plan.nfield, plan.npart, (int)plan.items.size(), plan.nsolve)));
+        carve(ctx->ws, plan.nfield, plan.npart, (int)plan.items.size(), plan.nsolve);
+        std::vector<SolveState> states(plan.nsolve);
+        for (size_t i = 0; i < plan.items.size(); i++)
+            for (int c = 0; c < plan.items[i].ncol; c++)
+                states[plan.items[i].solve0 + c] = fresh_state((int)i, c, jobs[i].tol);
+        int rc = upload(states);
+        if (rc) return rc;
+        for (size_t i = 0; i < jobs.size(); i++)
+            if ((rc = pack_source((int)i, jobs[i]))) return rc;
+        source_norms();
+        DDP_CUDA(ctx, cudaGetLastError());
+        if ((rc = build_loop_graph())) return rc;
         int cycles = 0;
-        bool all_done = false;
         for (int cyc = 0; cyc <= prm.max_outer; cyc++) {
-            // r64 = eta - D_Gamma x  (FP64 links, FP64 vectors).  At the first
-            // cycle x = 0, so r64 = eta and the partials of |eta|^2 are reused.
-            if (cyc > 0) {
-                hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A));
-                hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B));
-            }
-            fin<FIN_RESID>();
-            DDP_CUDA(ctx, cudaMemcpyAsync(h_st.data(), d_st, plan.nsolve * sizeof(SolveState),
-                                          cudaMemcpyDeviceToHost, st));
-            DDP_CUDA(ctx, cudaStreamSynchronize(st));
-            all_done = true;
+            residual(cyc == 0);
+            if ((rc = download_states())) return rc;
+            bool all_done = true;
             for (auto &S : h_st) all_done = all_done && S.outer_done;
             if (all_done || cyc == prm.max_outer) break;
             cycles++;
-            // normalised defect in storage format, even-odd right-hand side
-            conv(true, s, cyc ? re64 : be);
-            conv(true, ro, cyc ? ro64 : bo);
-            hop<P, EPI_AXPY_K, DOT_NORM>(hop_args(0, ro, r, s, none, none, A));  // r = r'_e + k H_eo r'_o
-            blas<P, OP_INIT>(A, 0);
-            DDP_CUDA(ctx, cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), st));
-            fin<FIN_INIT>();
-            DDP_CUDA(ctx, cudaGetLastError());
-            rc = run_inner();
-            if (rc) return rc;
-            hop<P, EPI_AXPY_K, DOT_NONE>(hop_args(1, xi, tmp, ro, none, none, A));  // e'_o = r'_o + k H_oe e'_e
-            conv(false, xi, xe);
-            conv(false, tmp, xo);
+            if ((rc = correction(cyc == 0))) return rc;
         }
-        // results
-        for (size_t i = 0; i < jobs.size(); i++) {
-            PackArgs pa;
-            memset(&pa, 0, sizeof(pa));
-            pa.it = plan.items[i];
-            pa.uout = (double2 *)jobs[i].out;
-            pa.fe = xe;
-            pa.fo = xo;
-            int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
-            k_unpack<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(pa);
-            launches++;
-        }
-        DDP_CUDA(ctx, cudaGetLastError());
-        DDP_CUDA(ctx, cudaStreamSynchronize(st));
+        for (size_t i = 0; i < jobs.size(); i++)
+            if ((rc = unpack_result((int)i, jobs[i].out))) return rc;
+        DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         infos.assign(jobs.size(), JobInfo());
         for (size_t i = 0; i < jobs.size(); i++) {
             const Item &it = plan.items[i];
@@ -345,6 +393,7 @@ struct Engine {
             inf.status = ok ? DDP_OK : DDP_ERR_NOT_CONVERGED;
         }
         ctx->launches += launches;
+        launches = 0;
         return DDP_OK;
     }
 };

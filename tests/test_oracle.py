@@ -423,3 +423,54 @@ def test_plaquette_equals_mean_link_to_the_fourth():
     P = synth.plaquette(synth.gauge_field(L, seed=synth.SEED_GAUGE), L)
     # 6 V plaquettes with single-plaquette std ~0.2: standard error ~0.0013
     assert abs(P - 0.59) < 0.005
+
+
+# ------------------------------------------------------------ two-level averaging
+
+def test_factorized_correlator_is_product_of_level1_means():
+    """Eq. factsing: the two traces are averaged separately over the level-1
+    variants and then multiplied (not the mean of the products)."""
+    rng = np.random.default_rng(3)
+    L0, vol3 = 6, 27.0
+    TA = rng.standard_normal((4, L0)) + 1j * rng.standard_normal((4, L0))
+    TB = rng.standard_normal((5, L0)) + 1j * rng.standard_normal((5, L0))
+    C = oracle.factorized_correlator(TA, TB, L0, vol3)
+    # identical variants reduce to the single-configuration product
+    C1 = oracle.factorized_correlator(TA[:1].repeat(3, 0), TB[:1].repeat(2, 0), L0, vol3)
+    assert np.allclose(C1, np.outer(TB[0], TA[0]) / vol3, rtol=1e-14, atol=0)
+    # order of the variants does not matter; bilinear in the two means
+    Cp = oracle.factorized_correlator(TA[::-1], TB[[2, 0, 4, 1, 3]], L0, vol3)
+    assert np.allclose(Cp, C, rtol=1e-13, atol=0)
+    C2 = oracle.factorized_correlator(2 * TA, TB, L0, vol3)
+    assert np.allclose(C2, 2 * C, rtol=1e-14, atol=0)
+    # it differs from the mean over variant pairs of the products when the regions correlate
+    pair_mean = np.mean([np.outer(TB[w], TA[v]) for v, w in zip(range(4), range(4))], axis=0) / vol3
+    assert not np.allclose(pair_mean, C)
+
+
+def test_noise_estimator_converges_to_trace():
+    """The diluted-noise time-slice trace averages to sum_x tr{g5 S(x,x)} (Sec. 5):
+    the off-diagonal terms carry random phases."""
+    L = (4, 2, 2, 2)
+    U = synth.gauge_field(L, seed=12)
+    o, e = (0, 0, 0, 0), L
+    n = int(np.prod(e))
+    D = dense.dirac_matrix(U, L, AP, 0.12)
+    Sinv = np.linalg.inv(D.toarray()).reshape(n, 12, n, 12)
+    g5 = np.kron(oracle.gamma()[4], np.eye(3))
+    exact = np.zeros(L[0], dtype=complex)
+    gi, _, _ = oracle.domain_maps(L, o, e)
+    for x in range(n):
+        exact[gi[x] // 8] += np.trace(g5 @ Sinv[x, :, x, :])
+    # Z2 x Z2 noise (|z| = 1) has no diagonal fluctuation: the estimate differs from the
+    # exact trace only by off-diagonal terms, whose average over sources vanishes
+    acc = np.zeros(L[0], dtype=complex)
+    nsrc = 200
+    rng = np.random.default_rng(5)
+    for i in range(nsrc):
+        z = (rng.choice([-1.0, 1.0], n) + 1j * rng.choice([-1.0, 1.0], n)) / np.sqrt(2)
+        eta = synth.diluted_noise_columns(z)
+        psi = np.einsum("xiyj,cyj->cxi", Sinv, eta.reshape(12, n, 12)).reshape(eta.shape)
+        acc += oracle.noise_trace(L, o, e, eta, psi)
+    est = acc / nsrc
+    assert np.abs(est - exact).max() < 0.25 * np.abs(exact).max()
