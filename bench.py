@@ -234,6 +234,8 @@ def run_gpu(args):
     prec = ddp.PRECISIONS[args.precision]
     U = synth.gauge_field(L, seed=synth.SEED_GAUGE + rank)
     ctx = ddp.ddp_create(torch.cuda.current_device(), torch.cuda.current_stream().cuda_stream)
+    if args.no_conditional:
+        ddp.ddp_set_param(ctx, "conditional", 0)
     wl = Workload(ddp, torch, ctx, prec, U)
     for _ in range(args.warmup):
         wl.step()
@@ -358,6 +360,8 @@ def main():
     ap.add_argument("--precision", default="fp16", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--no-conditional", action="store_true",
+                    help="run the inner loop as host-polled graph chunks (profilers see its kernels)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
