@@ -13,7 +13,7 @@ full lattice; per step:
 inputs resident in HBM; `e2e` runs the same step through the C ABI with host
 buffers (pinned), every transfer inside the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16|bf16|fp64]
   python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
 """
 from __future__ import annotations
@@ -236,6 +236,9 @@ def run_gpu(args):
     ctx = ddp.ddp_create(torch.cuda.current_device(), torch.cuda.current_stream().cuda_stream)
     if args.no_conditional:
         ddp.ddp_set_param(ctx, "conditional", 0)
+    for kv in args.param:
+        k, v = kv.split("=")
+        ddp.ddp_set_param(ctx, k, float(v))
     wl = Workload(ddp, torch, ctx, prec, U)
     for _ in range(args.warmup):
         wl.step()
@@ -357,9 +360,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp16", choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--param", action="append", default=[],
+                    help="solver parameter name=value passed to ddp_set_param (repeatable)")
     ap.add_argument("--no-conditional", action="store_true",
                     help="run the inner loop as host-polled graph chunks (profilers see its kernels)")
     args = ap.parse_args()

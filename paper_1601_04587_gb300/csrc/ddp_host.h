@@ -63,7 +63,7 @@ struct JobInfo {
 struct EngineParams {
     int max_outer = 40;
     int max_inner = 30000;
-    double floor_delta[4] = {1e-12, 2e-5, 2e-3, 2e-2};
+    double floor_delta[4] = {1e-12, 5e-6, 5e-4, 1e-2};
     int TS = 0, CG = 0;         // 0: heuristic
     int use_conditional = 1;    // device-driven while loop in a CUDA graph
     int host_chunk = 16;        // iterations per host check without conditional nodes
