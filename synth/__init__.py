@@ -269,3 +269,56 @@ def batch_boxes(L=BATCH_LATTICE):
 
 def box_center(box: Box):
     return tuple(box.origin[m] + box.extent[m] // 2 for m in range(4))
+
+
+# --- the same recipe with torch (CUDA or CPU), for the large lattices ----------------
+
+def _torch_gell_mann(torch, device):
+    return torch.from_numpy(_LAM).to(device)
+
+
+def random_su3_torch(n: int, eps: float, generator, device, chunk: int = 1 << 22):
+    """n links exp(i eps H) drawn with a torch.Generator (same law as random_su3)."""
+    import torch
+    lam = _torch_gell_mann(torch, device)
+    out = torch.empty((n, 3, 3), dtype=torch.complex128, device=device)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        h = torch.randn((b - a, 8), dtype=torch.float64, device=device, generator=generator)
+        H = torch.einsum("na,aij->nij", h.to(torch.complex128), lam) * 0.5
+        w, v = torch.linalg.eigh(H)
+        ph = torch.exp(1j * eps * w)
+        out[a:b] = torch.einsum("nij,nj,nkj->nik", v, ph, v.conj())
+    return out
+
+
+def gauge_field_torch(L, seed: int = SEED_GAUGE, device="cuda", eps: float | None = None):
+    """Seeded gauge field (4, V, 3, 3) complex128 on `device` (torch RNG stream)."""
+    import torch
+    if eps is None:
+        eps = tune_eps()
+    V = volume(L)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return random_su3_torch(4 * V, eps, g, device).reshape(4, V, 3, 3)
+
+
+def variant_field_torch(U_base, L, t_lo: int, t_hi: int, seed: int, eps: float | None = None):
+    """Torch version of variant_field: links with both ends in [t_lo, t_hi) redrawn,
+    the spatial links of the region's first slice frozen."""
+    import torch
+    if eps is None:
+        eps = tune_eps()
+    L = tuple(int(l) for l in L)
+    dev = U_base.device
+    U = U_base.clone()
+    slab = L[1] * L[2] * L[3]
+    t = torch.arange(volume(L), device=dev) // slab
+    in_region = (t >= t_lo) & (t < t_hi)
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+    for mu in range(4):
+        sel = in_region & ((t + 1 < t_hi) if mu == 0 else (t != t_lo))
+        idx = torch.nonzero(sel).flatten()
+        U[mu, idx] = random_su3_torch(idx.numel(), eps, g, dev)
+    return U

@@ -1,0 +1,261 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py times
+(GPU required).
+
+The oracle cannot solve every full-size column, so these tests check
+  - sampled columns the oracle can solve (small domains, one column),
+  - properties that hold at any size: the oracle's own D_Gamma applied to GPU
+    columns reproduces a relative residual <= 1e-10 for every sampled column,
+  - sampled series terms (bit-exact) and sampled time slices of the
+    correlators (same inputs, 1e-7),
+  - bit-exact index maps of the full-size domains.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+AP = oracle.BC_ANTIPERIODIC
+TOL = 1e-10
+COL_TOL = 1e-8
+CORR_TOL = 1e-7
+
+
+@pytest.fixture(scope="module")
+def ddp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_04587_gb300 import build
+    build.build()
+    import paper_1601_04587_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(ddp):
+    c = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    ddp.ddp_destroy(c)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _oracle_residual(U, L, box, kappa, eta_col, psi_col):
+    r = eta_col - oracle.apply_dirac(U, L, AP, box.origin, box.extent, kappa, psi_col)
+    return float(np.linalg.norm(r) / np.linalg.norm(eta_col))
+
+
+def _point_column(n, l, c):
+    e = np.zeros((n, 4, 3), dtype=np.complex128)
+    e[l, c // 3, c % 3] = 1.0
+    return e
+
+
+# --------------------------------------------------- 48 x 24^3 nested slabs (the bench workload)
+
+@pytest.fixture(scope="module")
+def slabs(ddp, ctx):
+    L = synth.SLAB_LATTICE
+    kappa = 0.14                     # the benchmark's kappa (see the design notes on its reading)
+    U = synth.gauge_field(L, seed=synth.SEED_GAUGE)
+    gid = ddp.ddp_load_gauge(ctx, torch.from_numpy(U).cuda(), L, ddp.DDP_BC_ANTIPERIODIC)
+    boxes = [synth.centered_time_slab(L, t, 0) for t in synth.SLAB_THICKNESS] + [synth.Box((0, 0, 0, 0), L)]
+    dids = [ddp.ddp_set_domain(ctx, gid, b.origin, b.extent) for b in boxes]
+    outs = [torch.zeros((12, b.n_sites, 4, 3), dtype=torch.complex128, device="cuda") for b in boxes]
+    reqs = [ddp.make_req(d, kappa, (0, 0, 0, 0), TOL, o) for d, o in zip(dids, outs)]
+    rc, infos = ddp.ddp_solve_batch(ctx, reqs, ddp.DDP_PREC_MIXED_FP32)
+    assert rc == ddp.DDP_OK
+    return L, U, kappa, boxes, dids, outs, infos
+
+
+def test_slab_maps_bit_exact(ddp, ctx, slabs):
+    L, U, kappa, boxes, dids, outs, infos = slabs
+    for b, d in zip(boxes, dids):
+        gi = np.zeros(b.n_sites, dtype=np.int64)
+        eo = np.zeros(b.n_sites, dtype=np.int64)
+        ddp.ddp_domain_sites(ctx, d, gi, eo)
+        rg, reo, _ = oracle.domain_maps(L, b.origin, b.extent)
+        assert np.array_equal(gi, rg) and np.array_equal(eo, reo)
+
+
+def test_slab_residuals_by_oracle_operator(slabs):
+    L, U, kappa, boxes, dids, outs, infos = slabs
+    for b, S, info in zip(boxes, outs, infos):
+        assert info.status == 0 and info.max_rel_residual <= TOL
+        l = oracle.local_index(L, b.origin, b.extent, (0, 0, 0, 0))
+        for c in (0, 7):                         # sampled columns
+            psi = S[c].cpu().numpy()
+            rr = _oracle_residual(U, L, b, kappa, _point_column(b.n_sites, l, c), psi)
+            assert rr <= TOL * 1.01, (b, c, rr)
+
+
+def test_slab_columns_against_oracle_solve(slabs):
+    L, U, kappa, boxes, dids, outs, infos = slabs
+    for b, S in zip(boxes[:2], outs[:2]):        # the two thinnest slabs: the oracle solves them in seconds
+        l = oracle.local_index(L, b.origin, b.extent, (0, 0, 0, 0))
+        c = 4
+        ref, it, rr, st = oracle.solve(U, L, AP, b.origin, b.extent, kappa,
+                                       _point_column(b.n_sites, l, c)[None], tol=1e-12)
+        assert st == 0
+        assert _rel(S[c].cpu().numpy(), ref[0]) < COL_TOL
+
+
+def test_slab_series_terms_bit_exact(ddp, ctx, slabs):
+    L, U, kappa, boxes, dids, outs, infos = slabs
+    for i in range(1, len(boxes)):
+        T = torch.zeros_like(outs[i])
+        ddp.ddp_series_terms(ctx, dids[i - 1], outs[i - 1], dids[i], outs[i], T, 12)
+        for c in (2, 11):
+            ref = oracle.series_term(L, boxes[i - 1].origin, boxes[i - 1].extent, outs[i - 1][c:c + 1].cpu().numpy(),
+                                     boxes[i].origin, boxes[i].extent, outs[i][c:c + 1].cpu().numpy())
+            assert np.array_equal(T[c:c + 1].cpu().numpy(), ref)
+
+
+def test_slab_correlators_on_sampled_slices(ddp, ctx, slabs):
+    L, U, kappa, boxes, dids, outs, infos = slabs
+    b, d, S = boxes[3], dids[3], outs[3]         # full lattice
+    C = np.zeros(2 * L[0])
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_NUCLEON, d, S, C)
+    P = np.zeros(2 * L[0])
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PION, d, S, P)
+    slab_n = L[1] * L[2] * L[3]
+    Sh = S.cpu().numpy()
+    for t in (0, 1, 17, 47):
+        sub = np.ascontiguousarray(Sh[:, t * slab_n:(t + 1) * slab_n])
+        o, e = (t, 0, 0, 0), (1,) + tuple(L[1:])
+        want_n = oracle.nucleon(L, o, e, sub)[t]
+        assert abs(complex(C[2 * t], C[2 * t + 1]) - want_n) <= CORR_TOL * abs(want_n)
+        want_p = oracle.pion(L, o, e, sub)[t]
+        assert abs(P[2 * t] - want_p) <= CORR_TOL * want_p
+
+
+# ------------------------------------------------ 32^4 batched uneven domains, stated kappa 0.155
+
+@pytest.fixture(scope="module")
+def lat32(ddp, ctx):
+    L = synth.BATCH_LATTICE
+    U = synth.gauge_field_torch(L, seed=synth.SEED_GAUGE, device="cuda")
+    gid = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
+    return L, U.cpu().numpy(), gid
+
+
+def test_batch_uneven_domains_stated_kappa(ddp, ctx, lat32):
+    """A sample of the uneven batch (8^4 blocks, 4x32^3 and 8x32^3 slabs) in one
+    batched launch at the stated kappa 0.155."""
+    L, U, gid = lat32
+    kappa = 0.155
+    boxes = synth.batch_boxes(L)
+    pick = [boxes[0], boxes[37], boxes[255], boxes[256], boxes[271], boxes[288]]   # 3 blocks, 2 thin, 1 thick slab
+    dids, outs, reqs, srcs = [], [], [], []
+    for b in pick:
+        d = ddp.ddp_set_domain(ctx, gid, b.origin, b.extent)
+        src = tuple((b.origin[m] + b.extent[m] // 2) % L[m] for m in range(4))
+        o = torch.zeros((12, b.n_sites, 4, 3), dtype=torch.complex128, device="cuda")
+        dids.append(d)
+        outs.append(o)
+        srcs.append(src)
+        reqs.append(ddp.make_req(d, kappa, src, TOL, o))
+    rc, infos = ddp.ddp_solve_batch(ctx, reqs, ddp.DDP_PREC_MIXED_FP32)
+    assert rc == ddp.DDP_OK, [ddp.info_dict(i) for i in infos]
+    for b, o, src, info in zip(pick, outs, srcs, infos):
+        assert info.max_rel_residual <= TOL
+        l = oracle.local_index(L, b.origin, b.extent, src)
+        rr = _oracle_residual(U, L, b, kappa, _point_column(b.n_sites, l, 5), o[5].cpu().numpy())
+        assert rr <= TOL * 1.01
+    # the 8^4 blocks: every column against the oracle
+    for b, o, src in zip(pick[:3], outs[:3], srcs[:3]):
+        ref, *_ = oracle.propagator(U, L, AP, b.origin, b.extent, kappa, src, tol=1e-12)
+        got = o.cpu().numpy()
+        assert max(_rel(got[c], ref[c]) for c in range(12)) < COL_TOL
+    # one block alone equals the same block inside the batch, bit for bit
+    one = torch.zeros_like(outs[1])
+    ddp.ddp_solve_propagator(ctx, dids[1], kappa, 0.0, srcs[1], TOL, ddp.DDP_PREC_MIXED_FP32, one)
+    assert torch.equal(one, outs[1])
+
+
+# ------------------------------------------- serving mix on the resident 32^4 field
+
+def test_serving_mix_full_size(ddp, ctx, lat32):
+    L, U, gid = lat32
+    specs = [(((3, 5, 7, 9), (4, 4, 4, 4)), 0.1555), (((8, 8, 8, 8), (8, 8, 8, 8)), 0.150),
+             (((12, 0, 0, 0), (4, 32, 32, 32)), 0.152), (((20, 0, 0, 0), (16, 32, 32, 32)), 0.142)]
+    ddp.ddp_serve_config(ctx, 24 << 30, 8, ddp.DDP_PREC_MIXED_FP32)
+    try:
+        outs, alone, tickets = [], [], []
+        for (o, e), kappa in specs:
+            d = ddp.ddp_set_domain(ctx, gid, o, e)
+            src = tuple((o[m] + e[m] // 2) % L[m] for m in range(4))
+            out = torch.zeros((12, int(np.prod(e)), 4, 3), dtype=torch.complex128, device="cuda")
+            rc, t = ddp.ddp_submit(ctx, ddp.make_req(d, kappa, src, TOL, out))
+            assert rc == ddp.DDP_OK
+            tickets.append(t)
+            outs.append(out)
+            one = torch.zeros_like(out)
+            alone.append((d, kappa, src, one))
+            ddp.ddp_serve_step(ctx)               # the next request joins a running batch
+        left, done = 1, {}
+        for _ in range(100):
+            left = ddp.ddp_serve_step(ctx)
+            for t in tickets:
+                if t not in done:
+                    f, info = ddp.ddp_poll(ctx, t)
+                    if f:
+                        done[t] = info
+            if left == 0 and len(done) == len(tickets):
+                break
+        assert len(done) == len(tickets)
+        for t, out, (d, kappa, src, one) in zip(tickets, outs, alone):
+            assert done[t].status == ddp.DDP_OK
+            ddp.ddp_solve_propagator(ctx, d, kappa, 0.0, src, TOL, ddp.DDP_PREC_MIXED_FP32, one)
+            assert torch.equal(out, one)
+    finally:
+        ddp.ddp_serve_reset(ctx)
+
+
+# ------------------------------------------------ 64 x 32^3 two-level (multi-level) workload
+
+def test_multilevel_full_size(ddp, ctx):
+    L = synth.MULTILEVEL_LATTICE
+    kappa = 0.14
+    nvar = 2
+    U0 = synth.gauge_field_torch(L, seed=synth.SEED_GAUGE, device="cuda")
+    gid0 = ddp.ddp_load_gauge(ctx, U0, L, ddp.DDP_BC_ANTIPERIODIC)
+    vol3 = float(L[1] * L[2] * L[3])
+    T = []
+    for r, (t_lo, t_hi) in enumerate([(0, 32), (32, 64)]):
+        box = synth.Box((t_lo, 0, 0, 0), (32, 32, 32, 32))
+        n = box.n_sites
+        z = synth.noise_field(n, synth.SEED_NOISE0 + r)
+        eta = synth.diluted_noise_columns(z)
+        eta_d = torch.from_numpy(eta).cuda()
+        sl = slice(t_lo * 32768, t_hi * 32768)
+        Tr = np.zeros((nvar, 2 * L[0]))
+        for v in range(nvar):
+            Uv = synth.variant_field_torch(U0, L, t_lo, t_hi, seed=synth.SEED_VARIANT0 + 100 * r + v)
+            vid = ddp.ddp_load_gauge_region(ctx, gid0, box.origin, box.extent, Uv[:, sl].contiguous())
+            d = ddp.ddp_set_domain(ctx, vid, box.origin, box.extent)
+            psi = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
+            rc, info = ddp.ddp_solve_sources(ctx, d, kappa, 0.0, eta_d, 12, TOL, ddp.DDP_PREC_MIXED_FP32, psi)
+            assert rc == ddp.DDP_OK
+            ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_NOISE, d, psi, Tr[v], eta=eta_d, ncol=12)
+            # sampled column: the oracle operator on the variant field reproduces the residual
+            Uvh = Uv.cpu().numpy()
+            psi_h = psi.cpu().numpy()
+            assert _oracle_residual(Uvh, L, box, kappa, eta[3], psi_h[3]) <= TOL * 1.01
+            # the time-slice traces of the GPU solution, recomputed by the oracle
+            want = oracle.noise_trace(L, box.origin, box.extent, eta, psi_h)
+            got = Tr[v, 0::2] + 1j * Tr[v, 1::2]
+            assert _rel(got, want) < CORR_TOL
+            ddp.ddp_free_domain(ctx, d)
+            ddp.ddp_free_gauge(ctx, vid)
+        T.append(Tr)
+    C = np.zeros(2 * L[0] * L[0])
+    ddp.ddp_factorized_correlator(ctx, T[0], nvar, T[1], nvar, L[0], vol3, C)
+    Cg = (C[0::2] + 1j * C[1::2]).reshape(L[0], L[0])
+    Co = oracle.factorized_correlator(T[0][:, 0::2] + 1j * T[0][:, 1::2], T[1][:, 0::2] + 1j * T[1][:, 1::2],
+                                      L[0], vol3)
+    assert _rel(Cg, Co) < CORR_TOL
