@@ -236,7 +236,8 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * (BiCGStab iterations per cycle), "delta_fp64" / "delta_fp32" /
  * "delta_fp16" / "delta_bf16" (smallest inner relative tolerance per storage
  * format), "tile_sites" (sites per block tile: 32; 0 = automatic),
- * "tile_cols" (columns per block, 1..12, 0 = automatic), "conditional" (1: the
+ * "tile_cols" (columns per block, 1..12, 0 = automatic), "tuned_cols_fp64" ...
+ * "tuned_cols_bf16" (a remembered autotuner choice, 0 = none), "conditional" (1: the
  * inner loop is a device-driven CUDA-graph WHILE node; 0: host-polled graph
  * chunks).  DDP_ERR_INVALID_ARG for unknown names or values. */
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value);
@@ -249,6 +250,13 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value);
  * the links touching the output sites). */
 int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters,
                  float *ms_per_launch, double *bytes_per_launch);
+
+/* Autotuner: times the inner-loop stencil on the domain (ncol columns, the
+ * given storage format, iters launches each) for every admissible number of
+ * columns per thread block, keeps the fastest for that storage format in the
+ * context (used by every later solve with that format) and returns it. */
+int ddp_autotune(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters, int *best_cols,
+                 float *best_ms);
 
 /* Number of kernels this context has launched so far. */
 long ddp_kernel_launches(const ddp_ctx *ctx);

@@ -90,6 +90,7 @@ def lib():
             "ddp_kernel_launches": ([vp], ctypes.c_long),
             "ddp_contract_static": ([i, i4, i4, i4, vp, vp, i, i4, vp, vp], i),
             "ddp_factorized_correlator": ([vp, vp, i, vp, i, i, d, vp], i),
+            "ddp_autotune": ([vp, i, d, i, i, i, i4, ctypes.POINTER(ctypes.c_float)], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -285,6 +286,39 @@ def ddp_time_hop(ctx, domain_id, kappa, ncol, precision, iters):
     _check(ctx, lib().ddp_time_hop(ctx, int(domain_id), float(kappa), int(ncol), int(precision), int(iters),
                                    ctypes.byref(ms), ctypes.byref(by)), "ddp_time_hop")
     return ms.value, by.value
+
+
+def ddp_autotune(ctx, domain_id, kappa, ncol, precision, iters=10):
+    best = ctypes.c_int()
+    ms = ctypes.c_float()
+    _check(ctx, lib().ddp_autotune(ctx, int(domain_id), float(kappa), int(ncol), int(precision), int(iters),
+                                   ctypes.byref(best), ctypes.byref(ms)), "ddp_autotune")
+    return best.value, ms.value
+
+
+_PREC_NAMES = {0: "fp64", 1: "fp32", 2: "fp16", 3: "bf16"}
+
+
+def autotune_cached(ctx, domain_id, n_sites, kappa, ncol, precision, cache_path=None, iters=10):
+    """ddp_autotune with a JSON cache keyed by storage format, columns and the
+    domain's size class (powers of two of its site count); the cache path defaults
+    to $DDP_TUNE_CACHE.  A cached choice is applied without timing."""
+    import json
+    path = cache_path or os.environ.get("DDP_TUNE_CACHE")
+    key = f"{_PREC_NAMES[int(precision)]}/ncol{int(ncol)}/sites2^{max(0, int(n_sites).bit_length() - 1)}"
+    cache = {}
+    if path and os.path.exists(path):
+        with open(path) as f:
+            cache = json.load(f)
+    if key in cache:
+        ddp_set_param(ctx, f"tuned_cols_{_PREC_NAMES[int(precision)]}", cache[key]["cols"])
+        return cache[key]["cols"], cache[key]["ms"]
+    cols, ms = ddp_autotune(ctx, domain_id, kappa, ncol, precision, iters)
+    if path:
+        cache[key] = {"cols": cols, "ms": ms}
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    return cols, ms
 
 
 def ddp_kernel_launches(ctx) -> int:

@@ -49,7 +49,8 @@ Arena::~Arena() {
 void make_plan(const std::vector<Job> &jobs, int prec, const EngineParams &prm, Plan &plan) {
     int maxcol = 1;
     for (auto &j : jobs) maxcol = std::max(maxcol, j.ncol);
-    int CG = std::min(prm.CG ? prm.CG : maxcol, HOP_MAX_CG);
+    int tuned = (prec >= 0 && prec < 4) ? prm.CG_prec[prec] : 0;
+    int CG = std::min(prm.CG ? prm.CG : (tuned ? tuned : maxcol), HOP_MAX_CG);
     int TS = HOP_TS;
     plan.TS = TS;
     plan.CG = CG;
@@ -846,10 +847,46 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
         if (value < 0 || value > HOP_MAX_CG) return DDP_ERR_INVALID_ARG;
         p.CG = (int)value;
     } else if (n == "conditional") p.use_conditional = value != 0;
+    else if (n == "tuned_cols_fp64" || n == "tuned_cols_fp32" || n == "tuned_cols_fp16" || n == "tuned_cols_bf16") {
+        if (value < 0 || value > HOP_MAX_CG) return DDP_ERR_INVALID_ARG;
+        int k = n == "tuned_cols_fp64" ? 0 : n == "tuned_cols_fp32" ? 1 : n == "tuned_cols_fp16" ? 2 : 3;
+        p.CG_prec[k] = (int)value;
+    }
     else return DDP_ERR_INVALID_ARG;
     return DDP_OK;
 }
 
 long ddp_kernel_launches(const ddp_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+// Autotuner: time the inner-loop stencil on the domain for every admissible
+// number of columns per block and keep the fastest for this storage format.
+int ddp_autotune(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters, int *best_cols,
+                 float *best_ms) {
+    if (!ctx || ncol < 1 || precision < 0 || precision > 3 || iters < 1) return DDP_ERR_INVALID_ARG;
+    const int cands[] = {12, 8, 6, 4, 3, 2, 1};
+    int saved = ctx->prm.CG, best = 0;
+    float bms = 0;
+    ctx->prm.CG = 0;
+    for (int c : cands) {
+        if (c > ncol) continue;
+        ctx->prm.CG = c;
+        float ms = 0;
+        double by = 0;
+        int rc = ddp_time_hop(ctx, domain_id, kappa, ncol, precision, iters, &ms, &by);
+        if (rc) {
+            ctx->prm.CG = saved;
+            return rc;
+        }
+        if (!best || ms < bms) {
+            best = c;
+            bms = ms;
+        }
+    }
+    ctx->prm.CG = saved;
+    ctx->prm.CG_prec[precision] = best;
+    if (best_cols) *best_cols = best;
+    if (best_ms) *best_ms = bms;
+    return DDP_OK;
+}
 
 }  // extern "C"

@@ -134,6 +134,91 @@ __device__ Cplx nucleon_site(const Cplx *site) {
     return csub(w1, w2);
 }
 
+// Nucleon per sink site, one warp per site.  With Gamma = C g5, which maps
+// spin rho to rho^1 with a phase, (Gamma M Gamma)_{rho sigma} = (-1)^(rho+sigma)
+// M_{rho^1, sigma^1}; with P- = (1 - g0)/2 of rank 2,
+//   (S^{be} P- S^{cf})_{alpha beta} = sum_{lambda=0,1} E_{alpha lambda} F_{lambda beta},
+//   E_{alpha lambda} = (S^{be}_{alpha lambda} - S^{be}_{alpha, lambda^2}) / 2,
+//   F_{lambda beta}  =  S^{cf}_{lambda beta} - S^{cf}_{lambda^2, beta},
+// so that with t_rho the row-rho parts of the traces,
+//   W_N1 = sum eps eps [sum_rho sum_sigma S^{ag}_{rho sigma} (-1)^(rho+sigma) S^{bf}_{rho^1 sigma^1}] tr[S^{ce} P-],
+//   W_N2 = sum eps eps  sum_rho sum_sigma S^{ag}_{rho sigma} (-1)^(rho+sigma) (E F)_{rho^1 sigma^1}.
+// The 36 epsilon pairs x 4 rows are spread over the 32 lanes.
+__device__ __forceinline__ Cplx sel(const Cplx *site, int rho, int a, int sigma, int b) {
+    return site[(3 * sigma + b) * 12 + 3 * rho + a];  // S(y,x)_{rho a, sigma b}
+}
+
+__device__ Cplx nucleon_unit(const Cplx *site, int unit) {
+    const int pr = unit >> 2, rho = unit & 3;
+    const int p1 = pr / 6, p2 = pr - 6 * (pr / 6);
+    const int a = kPerm[p1][0], b = kPerm[p1][1], c = kPerm[p1][2];
+    const int f = kPerm[p2][0], e = kPerm[p2][1], g = kPerm[p2][2];
+    const double sg = kSign[p1] * kSign[p2];
+    const int r1 = rho ^ 1;
+    // tr[S^{ce} P-]
+    Cplx t2 = {0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; k++) t2 = cadd(t2, csub(sel(site, k, c, k, e), sel(site, k, c, k ^ 2, e)));
+    t2 = cscale(0.5, t2);
+    // E_{rho^1, lambda}, lambda = 0, 1
+    Cplx E0 = cscale(0.5, csub(sel(site, r1, b, 0, e), sel(site, r1, b, 2, e)));
+    Cplx E1 = cscale(0.5, csub(sel(site, r1, b, 1, e), sel(site, r1, b, 3, e)));
+    Cplx t1 = {0, 0}, t3 = {0, 0};
+#pragma unroll
+    for (int sigma = 0; sigma < 4; sigma++) {
+        const int s1 = sigma ^ 1;
+        const double ph = ((rho + sigma) & 1) ? -1.0 : 1.0;
+        Cplx sag = cscale(ph, sel(site, rho, a, sigma, g));
+        t1 = cadd(t1, cmulc(sag, sel(site, r1, b, s1, f)));
+        Cplx F0 = csub(sel(site, 0, c, s1, f), sel(site, 2, c, s1, f));
+        Cplx F1 = csub(sel(site, 1, c, s1, f), sel(site, 3, c, s1, f));
+        t3 = cadd(t3, cmulc(sag, cadd(cmulc(E0, F0), cmulc(E1, F1))));
+    }
+    return cscale(sg, csub(cmulc(t1, t2), t3));
+}
+
+// grid (nchunk, e0), 128 threads: 4 warps x 8 sites = 32 sites of a time slice per block.
+constexpr int NUC_WARPS = 4, NUC_SITES_PER_WARP = 8;
+
+__global__ void __launch_bounds__(128) k_contract_nucleon(ContractArgs a) {
+    __shared__ Cplx s_site[NUC_WARPS][144];
+    __shared__ double s_re[NUC_WARPS], s_im[NUC_WARPS];
+    const Item &it = a.it;
+    const int slice_n = it.e[1] * it.e[2] * it.e[3];
+    const int n = 2 * it.nh;
+    const int t = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Cplx acc = {0, 0};
+    for (int j = 0; j < NUC_SITES_PER_WARP; j++) {
+        const int r = blockIdx.x * (NUC_WARPS * NUC_SITES_PER_WARP) + warp * NUC_SITES_PER_WARP + j;
+        if (r >= slice_n) break;
+        const int l = t * slice_n + r;
+        for (int q = lane; q < 144; q += 32) {
+            const int col = q / 12, k = q - 12 * (q / 12);
+            s_site[warp][q] = ld(a.S + ((int64_t)col * n + l) * 12 + k);
+        }
+        __syncwarp();
+        Cplx v = {0, 0};
+        for (int u = lane; u < 144; u += 32) v = cadd(v, nucleon_unit(s_site[warp], u));
+        acc = cadd(acc, v);
+        __syncwarp();
+    }
+    double re = warp_sum(acc.re), im = warp_sum(acc.im);
+    if (lane == 0) {
+        s_re[warp] = re;
+        s_im[warp] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0;
+        for (int w = 0; w < NUC_WARPS; w++) {
+            x += s_re[w];
+            y += s_im[w];
+        }
+        a.part[(int64_t)t * a.nchunk + blockIdx.x] = make_double2(x, y);
+    }
+}
+
 __device__ __forceinline__ void block_sum_to(double2 *dst, Cplx v) {
     __shared__ double sre[32], sim[32];
     double re = warp_sum(v.re), im = warp_sum(v.im);
@@ -341,14 +426,11 @@ extern "C" int ddp_contract(ddp_ctx *ctx, int kind, int domain_id, const double 
             a.kind = kind;
             a.nchunk = nchunk;
             a.part = (double2 *)dPart;
-            size_t smem = (kind == DDP_CONTRACT_NUCLEON) ? threads * 144 * sizeof(Cplx) : 0;
-            if (smem > 48 * 1024) {
-                if ((e = cudaFuncSetAttribute(k_contract_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem)) != cudaSuccess)
-                    break;
-            }
             dim3 grid(nchunk, d.e[0]);
-            k_contract_slice<<<grid, threads, smem, st>>>(a);
+            if (kind == DDP_CONTRACT_NUCLEON)
+                k_contract_nucleon<<<grid, NUC_WARPS * 32, 0, st>>>(a);
+            else
+                k_contract_slice<<<grid, threads, 0, st>>>(a);
             k_contract_final<<<g.L[0], 256, 0, st>>>(it, (const double2 *)dPart, nchunk, (double2 *)dOut);
             ctx->launches += 2;
         }
@@ -460,12 +542,11 @@ extern "C" int ddp_contract_static(int kind, const int L[4], const int origin[4]
     a.kind = kind;
     a.nchunk = nchunk;
     a.part = scratch;
-    size_t smem = (kind == DDP_CONTRACT_NUCLEON) ? threads * 144 * sizeof(Cplx) : 0;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_contract_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return DDP_ERR_CUDA;
     dim3 grid(nchunk, extent[0]);
-    k_contract_slice<<<grid, threads, smem, st>>>(a);
+    if (kind == DDP_CONTRACT_NUCLEON)
+        k_contract_nucleon<<<grid, NUC_WARPS * 32, 0, st>>>(a);
+    else
+        k_contract_slice<<<grid, threads, 0, st>>>(a);
     k_contract_final<<<L[0], 256, 0, st>>>(it, scratch, nchunk, (double2 *)C_out);
     return cudaGetLastError() == cudaSuccess ? DDP_OK : DDP_ERR_CUDA;
 }

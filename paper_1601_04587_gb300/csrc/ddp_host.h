@@ -65,6 +65,7 @@ struct EngineParams {
     int max_inner = 30000;
     double floor_delta[4] = {1e-12, 5e-6, 5e-4, 1e-2};
     int TS = 0, CG = 0;         // 0: heuristic
+    int CG_prec[4] = {0, 0, 0, 0};  // columns per block chosen by ddp_autotune, per storage format
     int use_conditional = 1;    // device-driven while loop in a CUDA graph
     int host_chunk = 16;        // iterations per host check without conditional nodes
 };

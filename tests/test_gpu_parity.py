@@ -292,3 +292,21 @@ def test_gauge_region_variant(ddp, ctx, field):
     assert _rel(outs[0], ref) < 1e-13
     ddp.ddp_free_gauge(ctx, vid)
     ddp.ddp_free_gauge(ctx, fid)
+
+
+def test_autotune_choice_keeps_results(ddp, ctx, field, tmp_path):
+    U, gid = field
+    o, e = BOXES[0]
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    cache = tmp_path / "tune.json"
+    cols, ms = ddp.autotune_cached(ctx, did, n, 0.124, 12, ddp.DDP_PREC_MIXED_FP32, str(cache), iters=3)
+    assert cols in (12, 8, 6, 4, 3, 2, 1) and ms > 0
+    again = ddp.autotune_cached(ctx, did, n, 0.124, 12, ddp.DDP_PREC_MIXED_FP32, str(cache))
+    assert again[0] == cols
+    S = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
+    rc, info = ddp.ddp_solve_propagator(ctx, did, 0.124, 0.0, (0, 0, 0, 0), 1e-10, 1, S)
+    assert rc == ddp.DDP_OK
+    ref, *_ = oracle.propagator(U, LAT, AP, o, e, 0.124, (0, 0, 0, 0), tol=1e-12)
+    assert max(_col_errors(S.cpu().numpy(), ref)) < COL_TOL
+    ddp.ddp_set_param(ctx, "tuned_cols_fp32", 0)
