@@ -237,10 +237,7 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * "delta_fp16" / "delta_bf16" (smallest inner relative tolerance per storage
  * format), "tile_sites" (sites per block tile: 32; 0 = automatic),
  * "tile_cols" (columns per block, 1..12, 0 = automatic), "tuned_cols_fp64" ...
- * "tuned_cols_bf16" (a remembered autotuner choice, 0 = none), "hop_table" (1: one-shot
- * solves precompute per-domain tables of oriented links and neighbour indices
- * instead of staging them per tile; also set by the environment variable
- * DDP_HOP_TABLE at ddp_create), "conditional" (1: the
+ * "tuned_cols_bf16" (a remembered autotuner choice, 0 = none), "conditional" (1: the
  * inner loop is a device-driven CUDA-graph WHILE node; 0: host-polled graph
  * chunks).  DDP_ERR_INVALID_ARG for unknown names or values. */
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value);

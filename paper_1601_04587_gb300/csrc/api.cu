@@ -6,7 +6,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <cstdlib>
 
 #include "ddp_host.h"
 
@@ -56,7 +55,7 @@ void make_plan(const std::vector<Job> &jobs, int prec, const EngineParams &prm, 
     plan.TS = TS;
     plan.CG = CG;
     plan.items.clear();
-    int64_t fbase = 0, pbase = 0, tbase = 0;
+    int64_t fbase = 0, pbase = 0;
     int blk = 0, solve = 0;
     for (auto &j : jobs) {
         Item it;
@@ -84,8 +83,6 @@ void make_plan(const std::vector<Job> &jobs, int prec, const EngineParams &prm, 
         it.links = j.g->links(prec);
         it.links64 = j.g->u64;
         it.gV = j.g->V;
-        it.tbase = tbase;
-        tbase += 16 * (int64_t)it.nh;
         blk += it.ntiles * it.ncg;
         solve += j.ncol;
         fbase += (int64_t)j.ncol * it.nh;
@@ -96,7 +93,6 @@ void make_plan(const std::vector<Job> &jobs, int prec, const EngineParams &prm, 
     plan.nsolve = solve;
     plan.nfield = std::max<int64_t>(fbase, 1);
     plan.npart = std::max<int64_t>(pbase, 1);
-    plan.nent = std::max<int64_t>(tbase, 1);
 }
 
 int solve_jobs_dispatch(ddp_ctx *ctx, int prec, std::vector<Job> &jobs, std::vector<JobInfo> &infos) {
@@ -380,7 +376,6 @@ int ddp_create(ddp_ctx **out, int device, void *stream) {
     }
     ddp_ctx *c = new ddp_ctx();
     c->device = device;
-    if (const char *ht = getenv("DDP_HOP_TABLE")) c->prm.hop_table = atoi(ht) != 0;
     c->user_stream = (cudaStream_t)stream;
     DeviceGuard dg(device);
     if (cudaFree(0) != cudaSuccess || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -852,7 +847,6 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
         if (value < 0 || value > HOP_MAX_CG) return DDP_ERR_INVALID_ARG;
         p.CG = (int)value;
     } else if (n == "conditional") p.use_conditional = value != 0;
-    else if (n == "hop_table") p.hop_table = value != 0;
     else if (n == "tuned_cols_fp64" || n == "tuned_cols_fp32" || n == "tuned_cols_fp16" || n == "tuned_cols_bf16") {
         if (value < 0 || value > HOP_MAX_CG) return DDP_ERR_INVALID_ARG;
         int k = n == "tuned_cols_fp64" ? 0 : n == "tuned_cols_fp32" ? 1 : n == "tuned_cols_fp16" ? 2 : 3;

@@ -324,25 +324,12 @@ struct Item {
     const void *links;    // links of the launch's storage precision
     const void *links64;  // FP64 links
     int64_t gV;           // lattice volume (link field row length)
-    int64_t tbase;        // first entry of the item in the hop tables (16 nh entries: parity, hop, site)
-};
-
-// Per-solve hop tables: for every (item, parity, hop d, even-odd site) the
-// neighbour's even-odd index (-1: hop dropped) and the oriented link with the
-// boundary factor folded in, in the compute precision, as 16-byte chunks
-// (FP32: 5 float4 holding 9 complex; FP64: 9 double2).  Entry
-// e = tbase + (8 parity + d) nh + h, chunk c at u[c * nent + e].
-struct HopTable {
-    int *nb;
-    void *u;
-    int64_t nent;
 };
 
 struct Launch {
     const Item *items;
     int nitems;
     int TS, CG;          // sites per tile (multiple of 32), columns per block
-    HopTable tab;        // tab.nb == nullptr: links staged per tile instead
 };
 
 // Locate the item owning block b (items sorted by blk0).

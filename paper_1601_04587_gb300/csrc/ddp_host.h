@@ -67,7 +67,6 @@ struct EngineParams {
     int TS = 0, CG = 0;         // 0: heuristic
     int CG_prec[4] = {0, 0, 0, 0};  // columns per block chosen by ddp_autotune, per storage format
     int use_conditional = 1;    // device-driven while loop in a CUDA graph
-    int hop_table = 0;          // 1: per-solve hop tables instead of per-tile link staging
     int host_chunk = 16;        // iterations per host check without conditional nodes
 };
 
@@ -160,7 +159,6 @@ struct Plan {
     std::vector<Item> items;
     int TS = 32, CG = 12;
     int64_t nfield = 0;    // site-columns per parity field
-    int64_t nent = 0;      // hop-table entries (16 per even-odd site pair)
     int64_t npart = 0;     // partial slots
     int nblocks = 0;
     int nsolve = 0;

@@ -133,83 +133,6 @@ __device__ __forceinline__ void load_item(const Launch &L, Item &dst) {
 // Tiles of TS sites: the links (oriented, boundary sign folded in, row 2
 // rebuilt) and neighbour indices of the tile's 8 TS hops are staged in shared
 // memory once and shared by the CG column-threads of every site.
-// Epilogue of the hopping kernels: out = combination of acc and same-parity
-// operands, stored in the storage format, plus the requested dot products.
-template <class P, int EPI, int DOT>
-__device__ __forceinline__ void hop_epilogue(const HopArgs &a, const Item &it, const TileCoord &tc,
-                                             const cx<typename P::real> acc[4][3], typename P::real &cre,
-                                             typename P::real &cim, typename P::real &nn) {
-    using R = typename P::real;
-        R o[24];
-    int64_t i = tc.cb + tc.h;
-    const R kap = (R)it.kappa;
-    if (EPI == EPI_PLAIN) {
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                o[2 * (3 * s + c)] = acc[s][c].re;
-                o[2 * (3 * s + c) + 1] = acc[s][c].im;
-            }
-    } else {
-        R w[24];
-        load_spinor<P>(a.v1, i, w);
-        R cw, ca;
-        if (EPI == EPI_MHAT) {
-            cw = R(1);
-            ca = -kap * kap;
-        } else if (EPI == EPI_AXPY_K) {
-            cw = R(1);
-            ca = kap;
-        } else if (EPI == EPI_DIRAC) {
-            cw = R(1) / (R(2) * kap);
-            ca = R(-0.5);
-        } else {  // EPI_RESID: eta - x/(2 kappa) + acc/2
-            cw = -R(1) / (R(2) * kap);
-            ca = R(0.5);
-        }
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                int j = 2 * (3 * s + c);
-                o[j] = cw * w[j] + ca * acc[s][c].re;
-                o[j + 1] = cw * w[j + 1] + ca * acc[s][c].im;
-            }
-        if (EPI == EPI_RESID) {
-            load_spinor<P>(a.v2, i, w);
-#pragma unroll
-            for (int j = 0; j < 24; j++) o[j] += w[j];
-        }
-        if (DOT == DOT_TS) {
-            // (t, s) = sum conj(t) s with t = out, s = v1 (reload v1: w was reused)
-            R s1[24];
-            load_spinor<P>(a.v1, i, s1);
-#pragma unroll
-            for (int j = 0; j < 12; j++) {
-                cre += o[2 * j] * s1[2 * j] + o[2 * j + 1] * s1[2 * j + 1];
-                cim += o[2 * j] * s1[2 * j + 1] - o[2 * j + 1] * s1[2 * j];
-            }
-        }
-    }
-    store_spinor<P>(a.out, i, o);
-    if (DOT == DOT_RHAT) {
-        R r[24];
-        load_spinor<P>(a.rh, i, r);
-#pragma unroll
-        for (int j = 0; j < 12; j++) {
-            cre += r[2 * j] * o[2 * j] + r[2 * j + 1] * o[2 * j + 1];
-            cim += r[2 * j] * o[2 * j + 1] - r[2 * j + 1] * o[2 * j];
-        }
-    }
-    if (DOT == DOT_TS || DOT == DOT_NORM) {
-        R s = 0;
-#pragma unroll
-        for (int j = 0; j < 24; j++) s += o[j] * o[j];
-        nn = s;
-    }
-    }
-
 // Tiles are exactly HOP_TS = 32 sites (one warp per column of a tile); a
 // block holds at most HOP_MAX_CG = 12 columns.
 constexpr int HOP_TS = 32;
@@ -274,98 +197,74 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
         DDP_HOP_STEP(6)
         DDP_HOP_STEP(7)
 #undef DDP_HOP_STEP
-        hop_epilogue<P, EPI, DOT>(a, it, tc, acc, cre, cim, nn);
-    }
-    if (DOT != DOT_NONE) block_partials(it, a.L, tc, cre, cim, nn, a.part, DOT == DOT_RHAT || DOT == DOT_TS,
-                                        DOT == DOT_TS || DOT == DOT_NORM);
-}
-
-// ------------------------------------------------ per-solve hop tables
-//
-// One thread per (parity, hop, site) of every item; blocks follow the tile grid
-// of the launch (only the first column group of each tile works).
-template <class P>
-__global__ void __launch_bounds__(256) k_build_hop_table(Launch L) {
-    using R = typename P::real;
-    using SU = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
-    constexpr int NSU = sizeof(R) == 4 ? 5 : 9;
-    __shared__ Item it;
-    load_item(L, it);
-    const int lb = blockIdx.x - it.blk0;
-    if (lb >= it.ntiles) return;  // other column groups of the tile: nothing to do
-    const int tile = lb;
-    for (int q = threadIdx.x; q < 16 * L.TS; q += blockDim.x) {
-        const int pd = q / L.TS, sidx = q - pd * L.TS;
-        const int par = pd >> 3, d = pd & 7;
-        const int h = tile * L.TS + sidx;
-        if (h >= it.nh) continue;
-        cx<R> u[3][3];
-        const int nb = stage_hop<P>(it, h, par, d, u);
-        const int64_t e = it.tbase + (int64_t)pd * it.nh + h;
-        L.tab.nb[e] = nb;
-        R flat[NSU * sizeof(SU) / sizeof(R)];
+        R o[24];
+        int64_t i = tc.cb + tc.h;
+        const R kap = (R)it.kappa;
+        if (EPI == EPI_PLAIN) {
 #pragma unroll
-        for (int k = 0; k < (int)(sizeof(flat) / sizeof(R)); k++) flat[k] = R(0);
-        if (nb >= 0) {
+            for (int s = 0; s < 4; s++)
 #pragma unroll
-            for (int k = 0; k < 9; k++) {
-                flat[2 * k] = u[k / 3][k % 3].re;
-                flat[2 * k + 1] = u[k / 3][k % 3].im;
+                for (int c = 0; c < 3; c++) {
+                    o[2 * (3 * s + c)] = acc[s][c].re;
+                    o[2 * (3 * s + c) + 1] = acc[s][c].im;
+                }
+        } else {
+            R w[24];
+            load_spinor<P>(a.v1, i, w);
+            R cw, ca;
+            if (EPI == EPI_MHAT) {
+                cw = R(1);
+                ca = -kap * kap;
+            } else if (EPI == EPI_AXPY_K) {
+                cw = R(1);
+                ca = kap;
+            } else if (EPI == EPI_DIRAC) {
+                cw = R(1) / (R(2) * kap);
+                ca = R(-0.5);
+            } else {  // EPI_RESID: eta - x/(2 kappa) + acc/2
+                cw = -R(1) / (R(2) * kap);
+                ca = R(0.5);
+            }
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    int j = 2 * (3 * s + c);
+                    o[j] = cw * w[j] + ca * acc[s][c].re;
+                    o[j + 1] = cw * w[j + 1] + ca * acc[s][c].im;
+                }
+            if (EPI == EPI_RESID) {
+                load_spinor<P>(a.v2, i, w);
+#pragma unroll
+                for (int j = 0; j < 24; j++) o[j] += w[j];
+            }
+            if (DOT == DOT_TS) {
+                // (t, s) = sum conj(t) s with t = out, s = v1 (reload v1: w was reused)
+                R s1[24];
+                load_spinor<P>(a.v1, i, s1);
+#pragma unroll
+                for (int j = 0; j < 12; j++) {
+                    cre += o[2 * j] * s1[2 * j] + o[2 * j + 1] * s1[2 * j + 1];
+                    cim += o[2 * j] * s1[2 * j + 1] - o[2 * j + 1] * s1[2 * j];
+                }
             }
         }
-        SU *dst = reinterpret_cast<SU *>(L.tab.u);
+        store_spinor<P>(a.out, i, o);
+        if (DOT == DOT_RHAT) {
+            R r[24];
+            load_spinor<P>(a.rh, i, r);
 #pragma unroll
-        for (int c = 0; c < NSU; c++) dst[(int64_t)c * L.tab.nent + e] = reinterpret_cast<const SU *>(flat)[c];
-    }
-}
-
-// The hopping kernel with its links and neighbours read from the hop tables:
-// no per-tile staging and no barrier before the gathers (the column-threads of
-// a site read the same table entries, served by L1).
-template <class P, int EPI, int DOT>
-__global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_hop_t(HopArgs a) {
-    using R = typename P::real;
-    using SU = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
-    constexpr int NSU = sizeof(R) == 4 ? 5 : 9;
-    __shared__ Item it;
-    load_item(a.L, it);
-    TileCoord tc = tile_coord(it, a.L);
-    if (a.skip && tc.valid && !a.st[it.solve0 + tc.col].active) tc.valid = false;
-    R cre = 0, cim = 0, nn = 0;
-    if (tc.valid) {
-        cx<R> acc[4][3];
-#pragma unroll
-        for (int s2 = 0; s2 < 4; s2++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) acc[s2][c] = mk<R>(0, 0);
-        const int64_t e0 = it.tbase + (int64_t)(8 * a.p) * it.nh + tc.h;
-        const SU *tu = reinterpret_cast<const SU *>(a.L.tab.u);
-#define DDP_HOP_STEP_T(D)                                                 \
-        {                                                                 \
-            const int64_t e = e0 + (int64_t)(D) * it.nh;                  \
-            const int nb = __ldg(a.L.tab.nb + e);                         \
-            if (nb >= 0) {                                                \
-                R flat[NSU * sizeof(SU) / sizeof(R)];                     \
-                _Pragma("unroll") for (int c = 0; c < NSU; c++)           \
-                    reinterpret_cast<SU *>(flat)[c] = __ldg(tu + (int64_t)c * a.L.tab.nent + e); \
-                cx<R> u[3][3];                                            \
-                _Pragma("unroll") for (int k = 0; k < 9; k++)             \
-                    u[k / 3][k % 3] = mk(flat[2 * k], flat[2 * k + 1]);   \
-                R v[24];                                                  \
-                load_spinor<P>(a.in, tc.cb + nb, v);                      \
-                hop_step<D>(v, u, acc);                                   \
-            }                                                             \
+            for (int j = 0; j < 12; j++) {
+                cre += r[2 * j] * o[2 * j] + r[2 * j + 1] * o[2 * j + 1];
+                cim += r[2 * j] * o[2 * j + 1] - r[2 * j + 1] * o[2 * j];
+            }
         }
-        DDP_HOP_STEP_T(0)
-        DDP_HOP_STEP_T(1)
-        DDP_HOP_STEP_T(2)
-        DDP_HOP_STEP_T(3)
-        DDP_HOP_STEP_T(4)
-        DDP_HOP_STEP_T(5)
-        DDP_HOP_STEP_T(6)
-        DDP_HOP_STEP_T(7)
-#undef DDP_HOP_STEP_T
-        hop_epilogue<P, EPI, DOT>(a, it, tc, acc, cre, cim, nn);
+        if (DOT == DOT_TS || DOT == DOT_NORM) {
+            R s = 0;
+#pragma unroll
+            for (int j = 0; j < 24; j++) s += o[j] * o[j];
+            nn = s;
+        }
     }
     if (DOT != DOT_NONE) block_partials(it, a.L, tc, cre, cim, nn, a.part, DOT == DOT_RHAT || DOT == DOT_TS,
                                         DOT == DOT_TS || DOT == DOT_NORM);

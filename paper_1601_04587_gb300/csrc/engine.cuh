@@ -30,13 +30,11 @@ struct Engine {
     FieldView be, bo, xe, xo, re64, ro64;      // FP64
     FieldView r, rh, p, v, s, t, xi, tmp, ro;  // storage format P
     Partials A, B;
-    HopTable tab = {nullptr, nullptr, 0}, tab64 = {nullptr, nullptr, 0};
-    bool use_table = false;
     Item *d_items = nullptr;
     SolveState *d_st = nullptr;
     LoopCtl *d_ctl = nullptr;
     std::vector<SolveState> h_st;
-    Launch L = {};
+    Launch L;
     int threads = 0;
     cudaGraphExec_t loop_exec = nullptr;
     cudaGraph_t loop_graph = nullptr;
@@ -65,39 +63,8 @@ struct Engine {
 
     template <class Q, int EPI, int DOT>
     void hop(const HopArgs &a) {
-        if (use_table) {
-            HopArgs b = a;
-            b.L.tab = Q::IS64 ? tab64 : tab;
-            k_hop_t<Q, EPI, DOT><<<plan.nblocks, threads, 0, ctx->stream>>>(b);
-        } else {
-            k_hop<Q, EPI, DOT><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
-        }
+        k_hop<Q, EPI, DOT><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
         launches++;
-    }
-
-    static size_t table_bytes(int64_t nent) {
-        size_t lo = P::IS64 ? 0 : (size_t)nent * 5 * sizeof(float4);
-        return (size_t)nent * sizeof(int) + lo + (size_t)nent * 9 * sizeof(double2) + 1024;
-    }
-
-    void carve_tables(Arena &a, int64_t nent) {
-        tab.nent = tab64.nent = nent;
-        tab.nb = tab64.nb = (int *)a.take(nent * sizeof(int));
-        tab64.u = a.take(nent * 9 * sizeof(double2));
-        tab.u = P::IS64 ? tab64.u : a.take(nent * 5 * sizeof(float4));
-    }
-
-    // Oriented links and neighbour indices of every item, once per solve.
-    void build_tables() {
-        Launch Lt = L;
-        Lt.tab = tab64;
-        k_build_hop_table<PF64><<<plan.nblocks, 256, 0, ctx->stream>>>(Lt);
-        launches++;
-        if (!P::IS64) {
-            Lt.tab = tab;
-            k_build_hop_table<P><<<plan.nblocks, 256, 0, ctx->stream>>>(Lt);
-            launches++;
-        }
     }
 
     template <class Q, int OP>
@@ -381,12 +348,8 @@ struct Engine {
     int run(std::vector<Job> &jobs, std::vector<JobInfo> &infos) {
         const EngineParams &prm = ctx->prm;
         make_plan(jobs, prec, prm, plan);
-        use_table = prm.hop_table != 0;
-        size_t tb = use_table ? table_bytes(plan.nent) : 0;
-        DDP_CUDA(ctx, ctx->ws.reserve(bytes_needed(plan.nfield, plan.npart, (int)plan.items.size(), plan.nsolve) +
-                                      tb));
+        DDP_CUDA(ctx, ctx->ws.reserve(bytes_needed(plan.nfield, plan.npart, (int)plan.items.size(), plan.nsolve)));
         carve(ctx->ws, plan.nfield, plan.npart, (int)plan.items.size(), plan.nsolve);
-        if (use_table) carve_tables(ctx->ws, plan.nent);
         std::vector<SolveState> states(plan.nsolve);
         for (size_t i = 0; i < plan.items.size(); i++)
             for (int c = 0; c < plan.items[i].ncol; c++)
@@ -395,7 +358,6 @@ struct Engine {
         if (rc) return rc;
         for (size_t i = 0; i < jobs.size(); i++)
             if ((rc = pack_source((int)i, jobs[i]))) return rc;
-        if (use_table) build_tables();
         source_norms();
         DDP_CUDA(ctx, cudaGetLastError());
         if ((rc = build_loop_graph())) return rc;
@@ -468,7 +430,7 @@ int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *ou
     int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
     unsigned nb = (unsigned)((nt + 255) / 256);
     k_pack_low<P><<<nb, 256, 0, st>>>(pa, ie, io);
-    Launch L = {};
+    Launch L;
     L.items = d_items;
     L.nitems = 1;
     L.TS = plan.TS;
@@ -509,19 +471,12 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, 
     Plan plan;
     make_plan(jobs, prec, ctx->prm, plan);
     const int64_t NF = plan.nfield;
-    const bool table = ctx->prm.hop_table != 0;
-    size_t need = 4 * field_bytes<P>(NF) + 2 * ((size_t)plan.npart * 24 + 1024) + sizeof(Item) + 1024 +
-                  (table ? Engine<P>::table_bytes(plan.nent) : 0);
+    size_t need = 4 * field_bytes<P>(NF) + 2 * ((size_t)plan.npart * 24 + 1024) + sizeof(Item) + 1024;
     DDP_CUDA(ctx, ctx->scratch.reserve(need));
     Arena &a = ctx->scratch;
     a.reset();
     FieldView in = carve_field<P>(a, NF), v1 = carve_field<P>(a, NF), rhv = carve_field<P>(a, NF),
               out = carve_field<P>(a, NF);
-    Engine<P> te;
-    te.ctx = ctx;
-    te.prec = prec;
-    te.plan = plan;
-    if (table) te.carve_tables(a, plan.nent);
     Partials A;
     A.c = (double2 *)a.take(plan.npart * sizeof(double2));
     A.n = (double *)a.take(plan.npart * sizeof(double));
@@ -537,7 +492,7 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, 
         DDP_CUDA(ctx, cudaMemsetAsync(v1.scale, 0, NF * sizeof(float), st));
         DDP_CUDA(ctx, cudaMemsetAsync(rhv.scale, 0, NF * sizeof(float), st));
     }
-    Launch L = {};
+    Launch L;
     L.items = d_items;
     L.nitems = 1;
     L.TS = plan.TS;
@@ -554,23 +509,12 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, 
     h.v2 = none;
     h.rh = rhv;
     h.part = A;
-    if (table) {
-        te.L = L;
-        te.build_tables();
-        h.L.tab = te.tab;
-    }
     cudaEvent_t e0, e1;
     DDP_CUDA(ctx, cudaEventCreate(&e0));
     DDP_CUDA(ctx, cudaEventCreate(&e1));
-    auto launch = [&]() {
-        if (table)
-            k_hop_t<P, EPI_MHAT, DOT_RHAT><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
-        else
-            k_hop<P, EPI_MHAT, DOT_RHAT><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
-    };
-    for (int i = 0; i < 3; i++) launch();
+    for (int i = 0; i < 3; i++) k_hop<P, EPI_MHAT, DOT_RHAT><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
     DDP_CUDA(ctx, cudaEventRecord(e0, st));
-    for (int i = 0; i < iters; i++) launch();
+    for (int i = 0; i < iters; i++) k_hop<P, EPI_MHAT, DOT_RHAT><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
     DDP_CUDA(ctx, cudaEventRecord(e1, st));
     DDP_CUDA(ctx, cudaEventSynchronize(e1));
     float t = 0;

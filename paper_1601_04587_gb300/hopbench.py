@@ -28,7 +28,6 @@ def main():
     ap.add_argument("--kappa", type=float, default=0.14)
     ap.add_argument("--tile-sites", type=int, default=0)
     ap.add_argument("--tile-cols", type=int, default=0)
-    ap.add_argument("--hop-table", action="store_true", help="per-solve hop tables instead of per-tile staging")
     args = ap.parse_args()
 
     import torch
@@ -43,15 +42,13 @@ def main():
         ddp.ddp_set_param(ctx, "tile_sites", args.tile_sites)
     if args.tile_cols:
         ddp.ddp_set_param(ctx, "tile_cols", args.tile_cols)
-    if args.hop_table:
-        ddp.ddp_set_param(ctx, "hop_table", 1)
     gid = ddp.ddp_load_gauge(ctx, torch.from_numpy(U).cuda(), L, ddp.DDP_BC_ANTIPERIODIC)
     did = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), L)
     ms, nbytes = ddp.ddp_time_hop(ctx, did, args.kappa, args.ncol, ddp.PRECISIONS[args.precision], args.iters)
     ddp.ddp_destroy(ctx)
     print(json.dumps({"lattice": L, "ncol": args.ncol, "precision": args.precision, "ms_per_launch": ms,
                       "algorithmic_bytes": nbytes, "GBps": nbytes / ms / 1e6,
-                      "tile_sites": args.tile_sites, "tile_cols": args.tile_cols, "hop_table": args.hop_table}))
+                      "tile_sites": args.tile_sites, "tile_cols": args.tile_cols}))
 
 
 if __name__ == "__main__":
