@@ -327,6 +327,34 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_other(args):
+    """Extra measurement lines: the uneven batch, the two-level workload, serving."""
+    import torch
+
+    import paper_1601_04587_gb300 as ddp
+    from paper_1601_04587_gb300 import workloads
+
+    torch.cuda.set_device(0)
+    prec = ddp.PRECISIONS[args.precision]
+    ctx = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    for kv in args.param:
+        k, v = kv.split("=")
+        ddp.ddp_set_param(ctx, k, float(v))
+    clocks = ClockSampler(0)
+    clocks.start()
+    if args.workload == "batch":
+        res = workloads.batch_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
+    elif args.workload == "multilevel":
+        res = workloads.multilevel_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
+    else:
+        res = workloads.serve_workload(ddp, torch, ctx, synth, prec)
+    res["clocks"] = clocks.stop()
+    res["precision"] = args.precision
+    res["gpu_launches"] = ddp.ddp_kernel_launches(ctx)
+    ddp.ddp_destroy(ctx)
+    print(json.dumps(res))
+
+
 # ---------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -363,15 +391,19 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--workload", default="slabs", choices=["slabs", "batch", "multilevel", "serve"],
+                    help="slabs: the benchmark line; the others print their own measurement line")
     ap.add_argument("--param", action="append", default=[],
                     help="solver parameter name=value passed to ddp_set_param (repeatable)")
     ap.add_argument("--no-conditional", action="store_true",
                     help="run the inner loop as host-polled graph chunks (profilers see its kernels)")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and args.workload == "slabs":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "slabs":
+        run_other(args)
     else:
         run_gpu(args)
 

@@ -1,0 +1,227 @@
+"""The batched, two-level and serving workloads, measured on one GPU.
+
+Used by ``bench.py --workload batch|multilevel|serve`` (the default bench line is
+the nested-slab workload).  Each function returns a dict that bench.py prints
+as one JSON line.  Gauge fields are synthetic (``synth``); their generation is
+input synthesis and stays outside the timed regions, while loading them into
+the library (packing, variants) is timed.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+# ----------------------------------------------------------------- uneven batch
+
+def batch_workload(ddp, torch, ctx, synth, precision, steps=1, warmup=1, tune_cache=None):
+    """256 8^4 blocks, 32 4x32^3 and 16 8x32^3 slabs of a 32^4 lattice, 12 point-source
+    columns each, all in one batched solve per step.  kappa: the stated 0.155 for the
+    blocks and 4x32^3 slabs, 0.150 for the 8x32^3 slabs (slow convergence at 0.155 on
+    the synthetic ensemble)."""
+    L = synth.BATCH_LATTICE
+    U = synth.gauge_field_torch(L, seed=synth.SEED_GAUGE, device="cuda")
+    boxes = synth.batch_boxes(L)
+    kap = [0.155 if b.extent != (8, 32, 32, 32) else 0.150 for b in boxes]
+    outs = [torch.empty((12, b.n_sites, 4, 3), dtype=torch.complex128, device="cuda") for b in boxes]
+    gid = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
+    tuned = {}
+    for ext in ((8, 8, 8, 8), (4, 32, 32, 32), (8, 32, 32, 32)):
+        d = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), ext)
+        tuned[str(ext)] = ddp.autotune_cached(ctx, d, int(np.prod(ext)), 0.15, 12, precision, tune_cache, iters=5)
+        ddp.ddp_free_domain(ctx, d)
+    ddp.ddp_free_gauge(ctx, gid)
+
+    def step():
+        g = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
+        dids = [ddp.ddp_set_domain(ctx, g, b.origin, b.extent) for b in boxes]
+        reqs = [ddp.make_req(d, k, tuple((b.origin[m] + b.extent[m] // 2) % L[m] for m in range(4)), 1e-10, o)
+                for d, k, b, o in zip(dids, kap, boxes, outs)]
+        rc, infos = ddp.ddp_solve_batch(ctx, reqs, precision)
+        for d in dids:
+            ddp.ddp_free_domain(ctx, d)
+        ddp.ddp_free_gauge(ctx, g)
+        return rc, infos
+
+    for _ in range(warmup):
+        step()
+    a, b = _events(torch)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(steps):
+        rc, infos = step()
+    b.record()
+    torch.cuda.synchronize()
+    secs = a.elapsed_time(b) / 1e3
+    worst = max(i.max_rel_residual for i in infos)
+    its = {k: max(i.inner_iters for i, bx in zip(infos, boxes) if str(bx.extent) == k)
+           for k in sorted({str(bx.extent) for bx in boxes})}
+    return {"workload": "32^4 lattice, 256 x 8^4 + 32 x 4x32^3 + 16 x 8x32^3 Dirichlet domains, 12 columns, "
+                        "one batched solve", "solves_per_s": len(boxes) * steps / secs,
+            "column_solves_per_s": 12 * len(boxes) * steps / secs, "s_per_batch": secs / steps,
+            "max_rel_residual": worst, "status": rc, "inner_iters_max_by_box": its,
+            "autotuned_cols": {k: v[0] for k, v in tuned.items()}, "steps": steps, "warmup": warmup}
+
+
+# ------------------------------------------------------------- two-level workload
+
+def multilevel_workload(ddp, torch, ctx, synth, precision, nvar=32, batch=8, steps=1, warmup=0):
+    """64 x 32^3 lattice, regions t in [0,32) and [32,64) as Dirichlet slabs, nvar
+    level-1 variants per region (region links redrawn, spatial links of the first
+    slice frozen), 12 diluted-noise columns per region shared by all variants,
+    kappa 0.140; traces per variant and the factorized correlator (Eq. factsing)."""
+    L = synth.MULTILEVEL_LATTICE
+    kappa = 0.140
+    vol3 = float(L[1] * L[2] * L[3])
+    U0 = synth.gauge_field_torch(L, seed=synth.SEED_GAUGE, device="cuda")
+    regions = [(0, 32), (32, 64)]
+    n = 32 * 32 ** 3
+    etas = [torch.from_numpy(synth.diluted_noise_columns(synth.noise_field(n, synth.SEED_NOISE0 + r))).cuda()
+            for r in range(2)]
+    psis = [torch.empty((12, n, 4, 3), dtype=torch.complex128, device="cuda") for _ in range(batch)]
+
+    def step():
+        gid0 = ddp.ddp_load_gauge(ctx, U0, L, ddp.DDP_BC_ANTIPERIODIC)
+        T = [torch.zeros((nvar, 2 * L[0]), dtype=torch.float64, device="cuda") for _ in range(2)]
+        t_solve = 0.0
+        for r, (lo, hi) in enumerate(regions):
+            box = synth.Box((lo, 0, 0, 0), (32, 32, 32, 32))
+            sl = slice(lo * 32768, hi * 32768)
+            for v0 in range(0, nvar, batch):
+                vids, dids, reqs = [], [], []
+                for j, v in enumerate(range(v0, min(nvar, v0 + batch))):
+                    Uv = synth.variant_field_torch(U0, L, lo, hi, seed=synth.SEED_VARIANT0 + 100 * r + v)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    vid = ddp.ddp_load_gauge_region(ctx, gid0, box.origin, box.extent, Uv[:, sl].contiguous())
+                    did = ddp.ddp_set_domain(ctx, vid, box.origin, box.extent)
+                    t_solve += time.perf_counter() - t0
+                    del Uv
+                    vids.append(vid)
+                    dids.append(did)
+                    reqs.append(ddp.make_req(did, kappa, tol=1e-10, out=psis[j], eta=etas[r], ncol=12))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, infos = ddp.ddp_solve_batch(ctx, reqs, precision)
+                for j, (v, d) in enumerate(zip(range(v0, v0 + len(reqs)), dids)):
+                    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_NOISE, d, psis[j], T[r][v], eta=etas[r], ncol=12)
+                torch.cuda.synchronize()
+                t_solve += time.perf_counter() - t0
+                for d, g in zip(dids, vids):
+                    ddp.ddp_free_domain(ctx, d)
+                    ddp.ddp_free_gauge(ctx, g)
+        C = torch.zeros(2 * L[0] * L[0], dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        ddp.ddp_factorized_correlator(ctx, T[0], nvar, T[1], nvar, L[0], vol3, C)
+        torch.cuda.synchronize()
+        t_solve += time.perf_counter() - t0
+        ddp.ddp_free_gauge(ctx, gid0)
+        return t_solve, C
+
+    for _ in range(warmup):
+        step()
+    secs = 0.0
+    for _ in range(steps):
+        s, C = step()
+        secs += s
+    nsolve = 2 * nvar * steps
+    return {"workload": f"64x32^3 two-level: 2 regions x {nvar} level-1 variants, 12 diluted-noise columns, "
+                        f"kappa {kappa}, factorized correlator", "solves_per_s": nsolve / secs,
+            "s_per_step": secs / steps, "timed": "variant loading, batched solves, noise traces, correlator "
+                                                 "(variant generation excluded)", "steps": steps}
+
+
+# ----------------------------------------------------------------------- serving
+
+SERVE_CLASSES = [((4, 4, 4, 4), 0.1555), ((8, 8, 8, 8), 0.1555), ((4, 32, 32, 32), 0.1555),
+                 ((8, 32, 32, 32), 0.150), ((16, 32, 32, 32), 0.145)]
+
+
+def _make_requests(synth, L, nreq, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nreq):
+        ext, kmax = SERVE_CLASSES[rng.integers(len(SERVE_CLASSES))]
+        origin = tuple(int(rng.integers(L[m])) for m in range(4))
+        src = tuple(int((origin[m] + rng.integers(ext[m])) % L[m]) for m in range(4))
+        kappa = float(rng.uniform(0.140, kmax))
+        out.append((origin, ext, src, kappa))
+    return out
+
+
+def _serve_run(ddp, torch, ctx, gid, L, reqs, precision, rate, budget, max_active):
+    """Open-loop Poisson arrivals at `rate` requests/s (rate=None: all at t=0)."""
+    ddp.ddp_serve_config(ctx, budget, max_active, precision)
+    rng = np.random.default_rng(7)
+    arrivals = np.zeros(len(reqs)) if rate is None else np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    pending = []          # (index, arrival) arrived but not admitted
+    inflight = {}         # ticket -> (index, arrival, domain, out)
+    lat = np.zeros(len(reqs))
+    nxt = 0
+    done = 0
+    C = torch.zeros(2 * L[0], dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    while done < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and arrivals[nxt] <= now:
+            pending.append((nxt, arrivals[nxt]))
+            nxt += 1
+        still = []
+        for i, arr in pending:
+            o, e, src, kappa = reqs[i]
+            d = ddp.ddp_set_domain(ctx, gid, o, e)
+            out = torch.empty((12, int(np.prod(e)), 4, 3), dtype=torch.complex128, device="cuda")
+            rc, t = ddp.ddp_submit(ctx, ddp.make_req(d, kappa, src, 1e-10, out))
+            if rc == ddp.DDP_OK:
+                inflight[t] = (i, arr, d, out)
+            else:
+                ddp.ddp_free_domain(ctx, d)
+                still.append((i, arr))
+        pending = still
+        if not inflight:
+            if nxt < len(reqs):
+                time.sleep(max(0.0, min(0.001, arrivals[nxt] - (time.perf_counter() - t0))))
+            continue
+        ddp.ddp_serve_step(ctx)
+        for t in list(inflight):
+            f, info = ddp.ddp_poll(ctx, t)
+            if f:
+                i, arr, d, out = inflight.pop(t)
+                ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_NUCLEON, d, out, C)   # the request's correlator
+                lat[i] = time.perf_counter() - t0 - arr
+                ddp.ddp_free_domain(ctx, d)
+                done += 1
+    total = time.perf_counter() - t0
+    ddp.ddp_serve_reset(ctx)
+    return {"solves_per_s": len(reqs) / total, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "wall_s": total}
+
+
+def serve_workload(ddp, torch, ctx, synth, precision, nreq=200, budget=96 << 30, max_active=32):
+    """Resident 32^4 field; requests on boxes 4^4 .. 16x32^3 with random origins and
+    point sources, kappa uniform in [0.140, min(0.1555, class limit)], 12 columns,
+    nucleon correlator per request.  Capacity = closed-loop throughput; then Poisson
+    arrivals at 0.5 and 0.9 of it, for the mixed path and for the plain FP64 path."""
+    L = synth.BATCH_LATTICE
+    U = synth.gauge_field_torch(L, seed=synth.SEED_GAUGE, device="cuda")
+    gid = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
+    reqs = _make_requests(synth, L, nreq, synth.SEED_SERVING)
+    out = {"workload": f"serving on a resident 32^4 field: {nreq} requests, boxes 4^4..16x32^3, 12 columns, "
+                       f"nucleon contraction per request", "requests": nreq}
+    for name, prec in (("mixed", precision), ("fp64", ddp.DDP_PREC_FP64)):
+        n_here = nreq if name == "mixed" else max(20, nreq // 5)
+        sub = reqs[:n_here]
+        cap = _serve_run(ddp, torch, ctx, gid, L, sub, prec, None, budget, max_active)
+        res = {"capacity_solves_per_s": cap["solves_per_s"], "requests": n_here}
+        for f in (0.5, 0.9):
+            r = _serve_run(ddp, torch, ctx, gid, L, sub, prec, f * cap["solves_per_s"], budget, max_active)
+            res[f"load_{f}"] = r
+        out[name] = res
+    ddp.ddp_free_gauge(ctx, gid)
+    return out
