@@ -22,6 +22,45 @@
 
 namespace ddp {
 
+// The pipelined stencil needs more than the default 48 KB of dynamic shared
+// memory: raise the limit once per instantiation, before any graph capture.
+template <class Q, int EPI, int DOT>
+inline void pipe_attr() {
+    if constexpr (!Q::IS64) {
+        static bool done = false;
+        if (!done) {
+            cudaFuncSetAttribute(k_hop_pipe<Q, EPI, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(PipeSmem<Q>));
+            done = true;
+        }
+    }
+}
+
+template <class P>
+inline void pipe_prepare() {
+    pipe_attr<P, EPI_PLAIN, DOT_NONE>();
+    pipe_attr<P, EPI_MHAT, DOT_RHAT>();
+    pipe_attr<P, EPI_MHAT, DOT_TS>();
+    pipe_attr<P, EPI_AXPY_K, DOT_NORM>();
+    pipe_attr<P, EPI_AXPY_K, DOT_NONE>();
+    pipe_attr<P, EPI_DIRAC, DOT_NONE>();
+}
+
+// One launch of the hopping term: the persistent pipelined kernel for the
+// FP32-compute formats when enabled, the per-tile kernel otherwise.
+template <class Q, int EPI, int DOT>
+inline void launch_hop(ddp_ctx *ctx, int nblocks, int threads, const HopArgs &a) {
+    if constexpr (!Q::IS64) {
+        if (ctx->prm.pipeline) {
+            pipe_attr<Q, EPI, DOT>();
+            int G = std::min(nblocks, std::max(1, ctx->num_sms) * 3);
+            k_hop_pipe<Q, EPI, DOT><<<G, threads, sizeof(PipeSmem<Q>), ctx->stream>>>(a, nblocks);
+            return;
+        }
+    }
+    k_hop<Q, EPI, DOT><<<nblocks, threads, 0, ctx->stream>>>(a);
+}
+
 template <class P>
 struct Engine {
     ddp_ctx *ctx;
@@ -63,7 +102,7 @@ struct Engine {
 
     template <class Q, int EPI, int DOT>
     void hop(const HopArgs &a) {
-        k_hop<Q, EPI, DOT><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
+        launch_hop<Q, EPI, DOT>(ctx, plan.nblocks, threads, a);
         launches++;
     }
 
@@ -360,6 +399,7 @@ struct Engine {
             if ((rc = pack_source((int)i, jobs[i]))) return rc;
         source_norms();
         DDP_CUDA(ctx, cudaGetLastError());
+        pipe_prepare<P>();
         if ((rc = build_loop_graph())) return rc;
         int cycles = 0;
         for (int cyc = 0; cyc <= prm.max_outer; cyc++) {
@@ -448,12 +488,12 @@ int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *ou
     h.in = io;
     h.out = oe;
     h.v1 = ie;
-    k_hop<P, EPI_DIRAC, DOT_NONE><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
+    launch_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
     h.p = 1;
     h.in = ie;
     h.out = oo;
     h.v1 = io;
-    k_hop<P, EPI_DIRAC, DOT_NONE><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
+    launch_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
     k_unpack_low<P><<<nb, 256, 0, st>>>(pa, oe, oo);
     ctx->launches += 4;
     DDP_CUDA(ctx, cudaGetLastError());
@@ -512,9 +552,9 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, 
     cudaEvent_t e0, e1;
     DDP_CUDA(ctx, cudaEventCreate(&e0));
     DDP_CUDA(ctx, cudaEventCreate(&e1));
-    for (int i = 0; i < 3; i++) k_hop<P, EPI_MHAT, DOT_RHAT><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
+    for (int i = 0; i < 3; i++) launch_hop<P, EPI_MHAT, DOT_RHAT>(ctx, plan.nblocks, plan.TS * plan.CG, h);
     DDP_CUDA(ctx, cudaEventRecord(e0, st));
-    for (int i = 0; i < iters; i++) k_hop<P, EPI_MHAT, DOT_RHAT><<<plan.nblocks, plan.TS * plan.CG, 0, st>>>(h);
+    for (int i = 0; i < iters; i++) launch_hop<P, EPI_MHAT, DOT_RHAT>(ctx, plan.nblocks, plan.TS * plan.CG, h);
     DDP_CUDA(ctx, cudaEventRecord(e1, st));
     DDP_CUDA(ctx, cudaEventSynchronize(e1));
     float t = 0;
