@@ -60,7 +60,9 @@ BOXES = [((0, 0, 0, 0), LAT),                    # whole lattice
          ((6, 0, 0, 0), (4, 4, 4, 6)),           # time slab across the antiperiodic boundary
          ((5, 1, 3, 2), (3, 2, 3, 4)),           # Dirichlet in every direction, wrapped, odd extents
          ((2, 3, 0, 5), (5, 4, 2, 2)),
-         ((1, 0, 0, 0), (8, 4, 4, 6))]           # full extent, shifted origin
+         ((1, 0, 0, 0), (8, 4, 4, 6)),           # full extent, shifted origin
+         ((7, 3, 1, 5), (1, 1, 1, 2)),           # two sites: every hop but one dropped
+         ((3, 0, 2, 0), (1, 4, 1, 6))]           # extent 1 in two directions
 
 
 # ------------------------------------------------------------------ index maps
@@ -310,3 +312,38 @@ def test_autotune_choice_keeps_results(ddp, ctx, field, tmp_path):
     ref, *_ = oracle.propagator(U, LAT, AP, o, e, 0.124, (0, 0, 0, 0), tol=1e-12)
     assert max(_col_errors(S.cpu().numpy(), ref)) < COL_TOL
     ddp.ddp_set_param(ctx, "tuned_cols_fp32", 0)
+
+
+@pytest.mark.parametrize("box,src", [(BOXES[5], (7, 3, 1, 5)), (BOXES[6], (3, 2, 2, 4))])
+def test_degenerate_boxes_solve(ddp, ctx, field, box, src):
+    U, gid = field
+    o, e = box
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    ref, *_ = oracle.propagator(U, LAT, AP, o, e, 0.124, src, tol=1e-12)
+    S = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
+    rc, info = ddp.ddp_solve_propagator(ctx, did, 0.124, 0.0, src, 1e-10, 1, S)
+    assert rc == ddp.DDP_OK
+    assert max(_col_errors(S.cpu().numpy(), ref)) < COL_TOL
+
+
+def test_zero_source_and_bad_kappa(ddp, ctx, field):
+    U, gid = field
+    o, e = BOXES[1]
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    eta = torch.zeros((3, n, 4, 3), dtype=torch.complex128, device="cuda")
+    eta[1, 5, 2, 1] = 1.0                      # one non-zero column among zero columns
+    out = torch.full_like(eta, float("nan"))
+    rc, info = ddp.ddp_solve_sources(ctx, did, 0.124, 0.0, eta, 3, 1e-10, 1, out)
+    assert rc == ddp.DDP_OK
+    got = out.cpu().numpy()
+    assert np.all(got[0] == 0) and np.all(got[2] == 0)
+    ref, *_ = oracle.solve(U, LAT, AP, o, e, 0.124, eta[1:2].cpu().numpy())
+    assert _rel(got[1], ref[0]) < COL_TOL
+    for bad in (0.0, -0.1, float("nan")):
+        with pytest.raises(ddp.DDPError) as ei:
+            ddp.ddp_solve_sources(ctx, did, bad, 0.0, eta, 3, 1e-10, 1, out)
+        assert ei.value.status == ddp.DDP_ERR_INVALID_ARG
+    with pytest.raises(ddp.DDPError):
+        ddp.ddp_solve_sources(ctx, did, 0.124, 0.0, eta, 3, 0.0, 1, out)      # tol must be positive

@@ -474,3 +474,17 @@ def test_noise_estimator_converges_to_trace():
         acc += oracle.noise_trace(L, o, e, eta, psi)
     est = acc / nsrc
     assert np.abs(est - exact).max() < 0.25 * np.abs(exact).max()
+
+
+def test_free_field_correlators_match_golden_values():
+    """Golden values written by tests/golden/make_golden.py from the momentum-space
+    closed form; the C oracle's solve + contractions must reproduce them."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "free_field_8x4x4x4.json")))
+    L = tuple(g["lattice"])
+    U = synth.unit_gauge_field(L)
+    S, *_ = oracle.propagator(U, L, AP, (0, 0, 0, 0), L, g["kappa"], (0, 0, 0, 0), tol=1e-13)
+    assert _rel(oracle.pion(L, (0, 0, 0, 0), L, S), np.array(g["pion"])) < 1e-11
+    want = np.array(g["nucleon_re"]) + 1j * np.array(g["nucleon_im"])
+    assert _rel(oracle.nucleon(L, (0, 0, 0, 0), L, S), want) < 1e-10
