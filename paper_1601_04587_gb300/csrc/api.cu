@@ -377,11 +377,9 @@ int ddp_create(ddp_ctx **out, int device, void *stream) {
     }
     ddp_ctx *c = new ddp_ctx();
     c->device = device;
-    if (const char *pl = getenv("DDP_PIPELINE")) c->prm.pipeline = atoi(pl) != 0;
     c->user_stream = (cudaStream_t)stream;
     DeviceGuard dg(device);
-    if (cudaFree(0) != cudaSuccess || cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) ||
-        cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaFree(0) != cudaSuccess || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -850,7 +848,6 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
         if (value < 0 || value > HOP_MAX_CG) return DDP_ERR_INVALID_ARG;
         p.CG = (int)value;
     } else if (n == "conditional") p.use_conditional = value != 0;
-    else if (n == "pipeline") p.pipeline = value != 0;
     else if (n == "tuned_cols_fp64" || n == "tuned_cols_fp32" || n == "tuned_cols_fp16" || n == "tuned_cols_bf16") {
         if (value < 0 || value > HOP_MAX_CG) return DDP_ERR_INVALID_ARG;
         int k = n == "tuned_cols_fp64" ? 0 : n == "tuned_cols_fp32" ? 1 : n == "tuned_cols_fp16" ? 2 : 3;

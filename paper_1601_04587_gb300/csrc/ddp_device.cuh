@@ -505,52 +505,6 @@ __device__ __forceinline__ int stage_hop(const Item &it, int h, int p, int d, cx
     return local_lex(it, kn) >> 1;
 }
 
-// Geometry of hop d from even-odd site h of parity p without touching the
-// link: the neighbour's even-odd index (-1: dropped), the link-field row of
-// the link used (U_mu(x) forward, U_mu(x - mu) backward), its direction mu and
-// the boundary factor f (+-1).
-__device__ __forceinline__ int hop_geometry(const Item &it, int h, int p, int d, int64_t *row, float *f) {
-    int k[4], x[4];
-    decode_site(it, h, p, k);
-#pragma unroll
-    for (int m = 0; m < 4; m++) {
-        int t = it.o[m] + k[m];
-        x[m] = (t >= it.L[m]) ? t - it.L[m] : t;
-    }
-    const int mu = d >> 1;
-    const bool fwd = !(d & 1);
-    int kn[4] = {k[0], k[1], k[2], k[3]};
-    bool ok = true;
-    const bool restricted = (it.rmask >> mu) & 1;
-    if (fwd) {
-        kn[mu] += 1;
-        if (restricted)
-            ok = kn[mu] < it.e[mu];
-        else if (kn[mu] == it.e[mu])
-            kn[mu] = 0;
-    } else {
-        kn[mu] -= 1;
-        if (restricted)
-            ok = kn[mu] >= 0;
-        else if (kn[mu] < 0)
-            kn[mu] = it.e[mu] - 1;
-    }
-    *f = 1.f;
-    if (mu == 0 && x[0] == (fwd ? it.L[0] - 1 : 0)) {
-        if (it.bc == 1) *f = -1.f;
-        if (it.bc == 2) ok = false;
-    }
-    if (!ok) return -1;
-    if (fwd) {
-        *row = link_row(it, x, p);
-    } else {
-        int xm[4] = {x[0], x[1], x[2], x[3]};
-        xm[mu] = (xm[mu] == 0) ? it.L[mu] - 1 : xm[mu] - 1;
-        *row = link_row(it, xm, p ^ 1);
-    }
-    return local_lex(it, kn) >> 1;
-}
-
 // acc += (1 -/+ g_mu) u psi for hop D (compile-time), link u already oriented.
 template <int D, typename R>
 __device__ __forceinline__ void hop_step(const R v[24], const cx<R> u[3][3], cx<R> acc[4][3]) {

@@ -67,7 +67,6 @@ struct EngineParams {
     int TS = 0, CG = 0;         // 0: heuristic
     int CG_prec[4] = {0, 0, 0, 0};  // columns per block chosen by ddp_autotune, per storage format
     int use_conditional = 1;    // device-driven while loop in a CUDA graph
-    int pipeline = 0;           // 1: persistent stencil with cp.async-prefetched links (FP32 compute)
     int host_chunk = 16;        // iterations per host check without conditional nodes
 };
 
@@ -110,7 +109,6 @@ struct ddp_ctx {
     void *serve = nullptr;
     // instrumentation: per-kernel-class launch counts of the last solve
     long launches = 0;
-    int num_sms = 0;
 };
 
 namespace ddp {

@@ -55,8 +55,8 @@ struct HopArgs {
     FieldView v2;   // second same-parity operand (EPI_RESID: eta)
     FieldView rh;   // shadow residual for DOT_RHAT
     Partials part;
-    const SolveState *st;  // with skip: columns whose solve is not active are left untouched
-    int skip;
+    const SolveState *st;  // skip 1: leave columns whose inner solve is not active untouched;
+    int skip;              // skip 2: leave columns whose outer solve has converged untouched
 };
 
 // Map a block/thread of a tile-structured launch to (item, column, site).
@@ -224,6 +224,17 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
     __shared__ R s_u[18][8 * TSMAX];
     load_item(a.L, it);
     const int TS = a.L.TS;
+    if (a.skip) {
+        // a block whose columns are all finished has nothing to stage or compute
+        const int cg = (blockIdx.x - it.blk0) / it.ntiles;
+        const int col = cg * a.L.CG + (int)threadIdx.x;
+        int live = 0;
+        if ((int)threadIdx.x < a.L.CG && col < it.ncol) {
+            const SolveState &S = a.st[it.solve0 + col];
+            live = (a.skip == 1) ? S.active : !S.outer_done;
+        }
+        if (!__syncthreads_or(live)) return;
+    }
     {
         const int tile = (blockIdx.x - it.blk0) % it.ntiles;
         for (int q = threadIdx.x; q < 8 * TS; q += blockDim.x) {
@@ -243,7 +254,10 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
     }
     __syncthreads();
     TileCoord tc = tile_coord(it, a.L);
-    if (a.skip && tc.valid && !a.st[it.solve0 + tc.col].active) tc.valid = false;
+    if (a.skip && tc.valid) {
+        const SolveState &S = a.st[it.solve0 + tc.col];
+        if ((a.skip == 1) ? !S.active : S.outer_done) tc.valid = false;
+    }
     R cre = 0, cim = 0, nn = 0;
     if (tc.valid) {
         cx<R> acc[4][3];
@@ -278,213 +292,6 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
     }
     if (DOT != DOT_NONE) block_partials(it, a.L, tc, cre, cim, nn, a.part, DOT == DOT_RHAT || DOT == DOT_TS,
                                         DOT == DOT_TS || DOT == DOT_NORM);
-}
-
-// ---------------------------------------------------- pipelined stencil
-//
-// Persistent form of k_hop for the FP32-compute formats: a block walks over
-// tiles (grid stride), and while it computes tile k the raw two-row links of
-// tile k+1 arrive in a second shared buffer through cp.async.  At the top of
-// each tile the raw links are rebuilt (row 2, orientation, boundary factor)
-// into the staged buffer read by the 12 column-threads.
-
-template <class P>
-struct RawLink;  // two rows of a link as stored
-template <>
-struct RawLink<PF32> {
-    float4 c[3];
-};
-template <>
-struct RawLink<PF16> {
-    uint2 c[3];
-};
-template <>
-struct RawLink<PBF16> {
-    uint2 c[3];
-};
-
-template <class P>
-struct PipeSmem {
-    Item it[2];
-    int info_nb[2][8 * HOP_TS];
-    int info_mu[2][8 * HOP_TS];  // mu | (backward << 2) | (negative factor << 3)
-    RawLink<P> raw[2][8 * HOP_TS];
-    int nb[8 * HOP_TS];
-    float u[18][8 * HOP_TS];
-};
-
-__device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-    if (bytes == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
-template <class P>
-__device__ __forceinline__ void pipe_issue(PipeSmem<P> &sm, int buf, const Launch &L, int b, int p) {
-    const Item &it = sm.it[buf];
-    const int tile = (b - it.blk0) % it.ntiles;
-    constexpr int CB = sizeof(((RawLink<P> *)0)->c[0]);
-    for (int q = threadIdx.x; q < 8 * L.TS; q += blockDim.x) {
-        const int d = q / L.TS, sidx = q - d * L.TS, h = tile * L.TS + sidx;
-        int nb = -1, code = 0;
-        if (h < it.nh) {
-            int64_t row;
-            float f;
-            nb = hop_geometry(it, h, p, d, &row, &f);
-            if (nb >= 0) {
-                const int mu = d >> 1;
-                code = mu | ((d & 1) << 2) | ((f < 0.f) << 3);
-                const char *base = reinterpret_cast<const char *>(it.links);
-#pragma unroll
-                for (int c = 0; c < 3; c++)
-                    cp_async(&sm.raw[buf][q].c[c], base + (((int64_t)mu * 3 + c) * it.gV + row) * CB, CB);
-            }
-        }
-        sm.info_nb[buf][q] = nb;
-        sm.info_mu[buf][q] = code;
-    }
-    cp_async_commit();
-}
-
-template <class P>
-__device__ __forceinline__ void raw_rows(const RawLink<P> &r, cx<float> u[3][3]);
-template <>
-__device__ __forceinline__ void raw_rows<PF32>(const RawLink<PF32> &r, cx<float> u[3][3]) {
-    u[0][0] = mk(r.c[0].x, r.c[0].y);
-    u[0][1] = mk(r.c[0].z, r.c[0].w);
-    u[0][2] = mk(r.c[1].x, r.c[1].y);
-    u[1][0] = mk(r.c[1].z, r.c[1].w);
-    u[1][1] = mk(r.c[2].x, r.c[2].y);
-    u[1][2] = mk(r.c[2].z, r.c[2].w);
-}
-template <>
-__device__ __forceinline__ void raw_rows<PF16>(const RawLink<PF16> &r, cx<float> u[3][3]) {
-    float2 a;
-    a = h2f(r.c[0].x); u[0][0] = mk(a.x, a.y);
-    a = h2f(r.c[0].y); u[0][1] = mk(a.x, a.y);
-    a = h2f(r.c[1].x); u[0][2] = mk(a.x, a.y);
-    a = h2f(r.c[1].y); u[1][0] = mk(a.x, a.y);
-    a = h2f(r.c[2].x); u[1][1] = mk(a.x, a.y);
-    a = h2f(r.c[2].y); u[1][2] = mk(a.x, a.y);
-}
-template <>
-__device__ __forceinline__ void raw_rows<PBF16>(const RawLink<PBF16> &r, cx<float> u[3][3]) {
-    float2 a;
-    a = b2f(r.c[0].x); u[0][0] = mk(a.x, a.y);
-    a = b2f(r.c[0].y); u[0][1] = mk(a.x, a.y);
-    a = b2f(r.c[1].x); u[0][2] = mk(a.x, a.y);
-    a = b2f(r.c[1].y); u[1][0] = mk(a.x, a.y);
-    a = b2f(r.c[2].x); u[1][1] = mk(a.x, a.y);
-    a = b2f(r.c[2].y); u[1][2] = mk(a.x, a.y);
-}
-
-template <class P>
-__device__ __forceinline__ void pipe_finish(PipeSmem<P> &sm, int buf, const Launch &L) {
-    for (int q = threadIdx.x; q < 8 * L.TS; q += blockDim.x) {
-        const int nb = sm.info_nb[buf][q];
-        sm.nb[q] = nb;
-        if (nb < 0) continue;
-        const int code = sm.info_mu[buf][q];
-        cx<float> v[3][3], u[3][3];
-        raw_rows<P>(sm.raw[buf][q], v);
-        reconstruct_row2(v);
-        const float f = (code & 8) ? -1.f : 1.f;
-        if (code & 4) {
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) u[i][j] = f * conj(v[j][i]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) u[i][j] = f * v[i][j];
-        }
-#pragma unroll
-        for (int k = 0; k < 9; k++) {
-            sm.u[2 * k][q] = u[k / 3][k % 3].re;
-            sm.u[2 * k + 1][q] = u[k / 3][k % 3].im;
-        }
-    }
-}
-
-template <class P, int EPI, int DOT>
-__global__ void __launch_bounds__(384, 3) k_hop_pipe(HopArgs a, int nblk) {
-    using R = float;
-    extern __shared__ __align__(16) unsigned char dsm[];
-    PipeSmem<P> &sm = *reinterpret_cast<PipeSmem<P> *>(dsm);
-    const int TS = a.L.TS;
-    int b = blockIdx.x, buf = 0;
-    if (b < nblk) {
-        if (threadIdx.x == 0) sm.it[0] = a.L.items[find_item(a.L.items, a.L.nitems, b)];
-        __syncthreads();
-        pipe_issue<P>(sm, 0, a.L, b, a.p);
-    }
-    while (b < nblk) {
-        const int b2 = b + gridDim.x;
-        cp_async_wait_all();
-        __syncthreads();
-        pipe_finish<P>(sm, buf, a.L);
-        if (threadIdx.x == 0 && b2 < nblk) sm.it[buf ^ 1] = a.L.items[find_item(a.L.items, a.L.nitems, b2)];
-        __syncthreads();
-        if (b2 < nblk) pipe_issue<P>(sm, buf ^ 1, a.L, b2, a.p);
-        const Item &it = sm.it[buf];
-        TileCoord tc;
-        {
-            const int lb = b - it.blk0;
-            tc.tile = lb % it.ntiles;
-            const int cg = lb / it.ntiles;
-            const int cl = threadIdx.x / TS;
-            const int sl0 = threadIdx.x - cl * TS;
-            tc.col = cg * a.L.CG + cl;
-            tc.h = tc.tile * TS + sl0;
-            tc.valid = (tc.col < it.ncol) && (tc.h < it.nh) && (cl < a.L.CG);
-            tc.cb = it.fbase + (int64_t)tc.col * it.nh;
-        }
-        if (a.skip && tc.valid && !a.st[it.solve0 + tc.col].active) tc.valid = false;
-        R cre = 0, cim = 0, nn = 0;
-        if (tc.valid) {
-            cx<R> acc[4][3];
-#pragma unroll
-            for (int s2 = 0; s2 < 4; s2++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) acc[s2][c] = mk<R>(0, 0);
-            const int sl = tc.h - tc.tile * TS;
-#define DDP_HOP_STEP_P(D)                                                 \
-            {                                                             \
-                const int q = (D) * TS + sl;                              \
-                const int nb = sm.nb[q];                                  \
-                if (nb >= 0) {                                            \
-                    R v[24];                                              \
-                    load_spinor<P>(a.in, tc.cb + nb, v);                  \
-                    cx<R> u[3][3];                                        \
-                    _Pragma("unroll") for (int k = 0; k < 9; k++)         \
-                        u[k / 3][k % 3] = mk(sm.u[2 * k][q], sm.u[2 * k + 1][q]); \
-                    hop_step<D>(v, u, acc);                               \
-                }                                                         \
-            }
-            DDP_HOP_STEP_P(0)
-            DDP_HOP_STEP_P(1)
-            DDP_HOP_STEP_P(2)
-            DDP_HOP_STEP_P(3)
-            DDP_HOP_STEP_P(4)
-            DDP_HOP_STEP_P(5)
-            DDP_HOP_STEP_P(6)
-            DDP_HOP_STEP_P(7)
-#undef DDP_HOP_STEP_P
-            hop_store_epilogue<P, EPI, DOT>(a, it, tc, acc, cre, cim, nn);
-        }
-        if (DOT != DOT_NONE) {
-            block_partials(it, a.L, tc, cre, cim, nn, a.part, DOT == DOT_RHAT || DOT == DOT_TS,
-                           DOT == DOT_TS || DOT == DOT_NORM, b);
-        }
-        b = b2;
-        buf ^= 1;
-    }
 }
 
 // ------------------------------------------------------------ vector updates
@@ -689,10 +496,15 @@ __global__ void __launch_bounds__(256) k_fin(FinArgs a) {
     const double2 zero = make_double2(0, 0), one = make_double2(1, 0);
     if (FIN == FIN_BNORM) {
         S.bnorm2 = n;
-        S.outer_done = (n == 0.0);
+        S.outer_done = S.outer_done || (n == 0.0);
     } else if (FIN == FIN_RESID) {
+        if (S.outer_done) {  // converged earlier: its residual was not recomputed
+            S.sigma = 0;
+            S.scale = 0;
+            return;
+        }
         S.rr64 = n;
-        bool done = S.outer_done || (n <= S.tol * S.tol * S.bnorm2) || !(n == n);
+        bool done = (n <= S.tol * S.tol * S.bnorm2) || !(n == n);
         S.outer_done = done ? 1 : 0;
         if (done) {
             S.sigma = 0;

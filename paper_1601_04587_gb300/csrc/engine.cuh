@@ -22,42 +22,9 @@
 
 namespace ddp {
 
-// The pipelined stencil needs more than the default 48 KB of dynamic shared
-// memory: raise the limit once per instantiation, before any graph capture.
-template <class Q, int EPI, int DOT>
-inline void pipe_attr() {
-    if constexpr (!Q::IS64) {
-        static bool done = false;
-        if (!done) {
-            cudaFuncSetAttribute(k_hop_pipe<Q, EPI, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(PipeSmem<Q>));
-            done = true;
-        }
-    }
-}
-
-template <class P>
-inline void pipe_prepare() {
-    pipe_attr<P, EPI_PLAIN, DOT_NONE>();
-    pipe_attr<P, EPI_MHAT, DOT_RHAT>();
-    pipe_attr<P, EPI_MHAT, DOT_TS>();
-    pipe_attr<P, EPI_AXPY_K, DOT_NORM>();
-    pipe_attr<P, EPI_AXPY_K, DOT_NONE>();
-    pipe_attr<P, EPI_DIRAC, DOT_NONE>();
-}
-
-// One launch of the hopping term: the persistent pipelined kernel for the
-// FP32-compute formats when enabled, the per-tile kernel otherwise.
+// One launch of the hopping term.
 template <class Q, int EPI, int DOT>
 inline void launch_hop(ddp_ctx *ctx, int nblocks, int threads, const HopArgs &a) {
-    if constexpr (!Q::IS64) {
-        if (ctx->prm.pipeline) {
-            pipe_attr<Q, EPI, DOT>();
-            int G = std::min(nblocks, std::max(1, ctx->num_sms) * 3);
-            k_hop_pipe<Q, EPI, DOT><<<G, threads, sizeof(PipeSmem<Q>), ctx->stream>>>(a, nblocks);
-            return;
-        }
-    }
     k_hop<Q, EPI, DOT><<<nblocks, threads, 0, ctx->stream>>>(a);
 }
 
@@ -344,8 +311,8 @@ struct Engine {
     void residual(bool skip_hop) {
         FieldView none = {nullptr, nullptr, 0};
         if (!skip_hop) {
-            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A));
-            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B));
+            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A, 2));
+            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B, 2));
         }
         fin<FIN_RESID>();
     }
@@ -399,7 +366,6 @@ struct Engine {
             if ((rc = pack_source((int)i, jobs[i]))) return rc;
         source_norms();
         DDP_CUDA(ctx, cudaGetLastError());
-        pipe_prepare<P>();
         if ((rc = build_loop_graph())) return rc;
         int cycles = 0;
         for (int cyc = 0; cyc <= prm.max_outer; cyc++) {

@@ -166,7 +166,6 @@ struct Server : ServerBase {
             DDP_CUDA(ctx, cudaMemcpyAsync(eng.d_st, eng.h_st.data(), eng.plan.nsolve * sizeof(SolveState),
                                           cudaMemcpyHostToDevice, ctx->stream));
             eng.drop_graph();
-            pipe_prepare<P>();
             if ((rc = eng.build_loop_graph())) return rc;
             if ((rc = eng.correction(false))) return rc;
             if ((rc = eng.download_states())) return rc;
