@@ -379,6 +379,14 @@ int ddp_create(ddp_ctx **out, int device, void *stream) {
     c->device = device;
     c->user_stream = (cudaStream_t)stream;
     DeviceGuard dg(device);
+    // staging buffers of host-memory arguments come from the device's stream-ordered
+    // pool; keep freed blocks in the pool instead of returning them at every sync
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
     if (cudaFree(0) != cudaSuccess || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
@@ -397,6 +405,9 @@ int ddp_destroy(ddp_ctx *ctx) {
     DeviceGuard dg(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ddp_serve_reset(ctx);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    cudaGetLastError();
     for (auto &kv : ctx->gauges) {
         cudaFree(kv.second->u64);
         cudaFree(kv.second->u32);
