@@ -188,6 +188,33 @@ __device__ __forceinline__ void load_spinor<PBF16>(const FieldView &f, int64_t i
     }
 }
 
+// Spinor as stored: FP16 values without their site-column scale, which is
+// returned in *s (1 for the other formats).
+template <class P>
+__device__ __forceinline__ void load_spinor_raw(const FieldView &f, int64_t i, typename P::real v[24],
+                                                typename P::real *s) {
+    load_spinor<P>(f, i, v);
+    *s = typename P::real(1);
+}
+template <>
+__device__ __forceinline__ void load_spinor_raw<PF16>(const FieldView &f, int64_t i, float v[24], float *s) {
+    const uint4 *b = reinterpret_cast<const uint4 *>(f.p);
+    *s = __ldg(f.scale + i);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        uint4 c = __ldg(b + j * f.stride + i);
+        float2 a0 = h2f(c.x), a1 = h2f(c.y), a2 = h2f(c.z), a3 = h2f(c.w);
+        v[8 * j + 0] = a0.x;
+        v[8 * j + 1] = a0.y;
+        v[8 * j + 2] = a1.x;
+        v[8 * j + 3] = a1.y;
+        v[8 * j + 4] = a2.x;
+        v[8 * j + 5] = a2.y;
+        v[8 * j + 6] = a3.x;
+        v[8 * j + 7] = a3.y;
+    }
+}
+
 template <class P>
 __device__ __forceinline__ void store_spinor(const FieldView &f, int64_t i, const typename P::real v[24]);
 
@@ -381,12 +408,33 @@ __device__ __forceinline__ int64_t link_row(const Item &it, const int x[4], int 
 // and (1 + g)psi = [h; A^+ h] with h = psi_up + A psi_dn, so only the two
 // rows of h are multiplied by the link.
 
-template <typename R>
+// w = u h.  FMA: one multiply-add chain per real component (6 instructions
+// instead of 8); it saves issue slots where the kernel is issue-bound (16-bit
+// storage) but holds more registers live, so the FP32-storage stencil keeps
+// the plain form.
+template <bool FMA, typename R>
 __device__ __forceinline__ void su3_mul_half(const cx<R> u[3][3], const cx<R> h[2][3], cx<R> w[2][3]) {
 #pragma unroll
     for (int s = 0; s < 2; s++)
 #pragma unroll
-        for (int a = 0; a < 3; a++) w[s][a] = u[a][0] * h[s][0] + u[a][1] * h[s][1] + u[a][2] * h[s][2];
+        for (int a = 0; a < 3; a++) {
+            if (FMA) {
+                R re = u[a][0].re * h[s][0].re;
+                R im = u[a][0].re * h[s][0].im;
+                re = fma(-u[a][0].im, h[s][0].im, re);
+                im = fma(u[a][0].im, h[s][0].re, im);
+#pragma unroll
+                for (int b = 1; b < 3; b++) {
+                    re = fma(u[a][b].re, h[s][b].re, re);
+                    im = fma(u[a][b].re, h[s][b].im, im);
+                    re = fma(-u[a][b].im, h[s][b].im, re);
+                    im = fma(u[a][b].im, h[s][b].re, im);
+                }
+                w[s][a] = mk(re, im);
+            } else {
+                w[s][a] = u[a][0] * h[s][0] + u[a][1] * h[s][1] + u[a][2] * h[s][2];
+            }
+        }
 }
 template <typename R>
 __device__ __forceinline__ void su3_adj_mul_half(const cx<R> u[3][3], const cx<R> h[2][3], cx<R> w[2][3]) {
@@ -422,26 +470,33 @@ __device__ __forceinline__ void project(const R v[24], cx<R> h[2][3]) {
     }
 }
 
-// acc += f * [w; lower(w)] for direction MU and hop sense FWD.
+// acc += f * [w; lower(w)] for direction MU and hop sense FWD, each real
+// component one multiply-add (f is 1 for unscaled storage, the site-column
+// scale for FP16).
+template <typename R>
+__device__ __forceinline__ void cfma(cx<R> &acc, R f, cx<R> w) {
+    acc.re = fma(f, w.re, acc.re);
+    acc.im = fma(f, w.im, acc.im);
+}
 template <int MU, bool FWD, typename R>
 __device__ __forceinline__ void accumulate(cx<R> acc[4][3], const cx<R> w[2][3], R f) {
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        cx<R> w0 = f * w[0][a], w1 = f * w[1][a];
-        acc[0][a] = acc[0][a] + w0;
-        acc[1][a] = acc[1][a] + w1;
+        const cx<R> w0 = w[0][a], w1 = w[1][a];
+        cfma(acc[0][a], f, w0);
+        cfma(acc[1][a], f, w1);
         if (MU == 0) {
-            acc[2][a] = FWD ? acc[2][a] - w0 : acc[2][a] + w0;
-            acc[3][a] = FWD ? acc[3][a] - w1 : acc[3][a] + w1;
+            cfma(acc[2][a], FWD ? -f : f, w0);
+            cfma(acc[3][a], FWD ? -f : f, w1);
         } else if (MU == 1) {
-            acc[2][a] = FWD ? acc[2][a] + mul_mi(w1) : acc[2][a] + mul_i(w1);
-            acc[3][a] = FWD ? acc[3][a] + mul_mi(w0) : acc[3][a] + mul_i(w0);
+            cfma(acc[2][a], f, FWD ? mul_mi(w1) : mul_i(w1));
+            cfma(acc[3][a], f, FWD ? mul_mi(w0) : mul_i(w0));
         } else if (MU == 2) {
-            acc[2][a] = FWD ? acc[2][a] - w1 : acc[2][a] + w1;
-            acc[3][a] = FWD ? acc[3][a] + w0 : acc[3][a] - w0;
+            cfma(acc[2][a], FWD ? -f : f, w1);
+            cfma(acc[3][a], FWD ? f : -f, w0);
         } else {
-            acc[2][a] = FWD ? acc[2][a] + mul_mi(w0) : acc[2][a] + mul_i(w0);
-            acc[3][a] = FWD ? acc[3][a] + mul_i(w1) : acc[3][a] + mul_mi(w1);
+            cfma(acc[2][a], f, FWD ? mul_mi(w0) : mul_i(w0));
+            cfma(acc[3][a], f, FWD ? mul_i(w1) : mul_mi(w1));
         }
     }
 }
@@ -505,15 +560,16 @@ __device__ __forceinline__ int stage_hop(const Item &it, int h, int p, int d, cx
     return local_lex(it, kn) >> 1;
 }
 
-// acc += (1 -/+ g_mu) u psi for hop D (compile-time), link u already oriented.
-template <int D, typename R>
-__device__ __forceinline__ void hop_step(const R v[24], const cx<R> u[3][3], cx<R> acc[4][3]) {
+// acc += f (1 -/+ g_mu) u psi for hop D (compile-time), link u already
+// oriented; f is the FP16 site-column scale of psi, else 1.
+template <int D, bool FMA, typename R>
+__device__ __forceinline__ void hop_step(const R v[24], const cx<R> u[3][3], cx<R> acc[4][3], R f) {
     constexpr int MU = D >> 1;
     constexpr bool FWD = !(D & 1);
     cx<R> h[2][3], w[2][3];
     project<MU, FWD>(v, h);
-    su3_mul_half(u, h, w);
-    accumulate<MU, FWD>(acc, w, R(1));
+    su3_mul_half<FMA>(u, h, w);
+    accumulate<MU, FWD>(acc, w, f);
 }
 
 // --------------------------------------------------------- reductions

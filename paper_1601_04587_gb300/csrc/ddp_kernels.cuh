@@ -3,6 +3,8 @@
 // updates, FP64 defect-correction steps and layout conversions.
 #pragma once
 
+#include <type_traits>
+
 #include "ddp_device.cuh"
 
 namespace ddp {
@@ -210,6 +212,26 @@ __device__ __forceinline__ void hop_store_epilogue(const HopArgs &a, const Item 
     }
     }
 
+// A staged link in shared memory: 9 complex, one 8-byte (FP32 compute) or
+// 16-byte (FP64) access each.
+template <typename R>
+__device__ __forceinline__ void put_link(R *d, const cx<R> u[3][3]) {
+    using V2 = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    V2 *q = reinterpret_cast<V2 *>(d);
+#pragma unroll
+    for (int k = 0; k < 9; k++) q[k] = V2{u[k / 3][k % 3].re, u[k / 3][k % 3].im};
+}
+template <typename R>
+__device__ __forceinline__ void get_link(const R *d, cx<R> u[3][3]) {
+    using V2 = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const V2 *q = reinterpret_cast<const V2 *>(d);
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const V2 c = q[k];
+        u[k / 3][k % 3] = mk(c.x, c.y);
+    }
+}
+
 // Tiles are exactly HOP_TS = 32 sites (one warp per column of a tile); a
 // block holds at most HOP_MAX_CG = 12 columns.
 constexpr int HOP_TS = 32;
@@ -220,8 +242,11 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
     using R = typename P::real;
     constexpr int TSMAX = HOP_TS;
     __shared__ Item it;
+    // oriented link of hop slot q at s_u[q * 18]: 9 complex; vector reads of
+    // consecutive slots by a warp fall in distinct banks
+    constexpr int LP = 18;
     __shared__ int s_nb[8 * TSMAX];
-    __shared__ R s_u[18][8 * TSMAX];
+    __shared__ __align__(16) R s_u[8 * TSMAX * LP];
     load_item(a.L, it);
     const int TS = a.L.TS;
     if (a.skip) {
@@ -243,13 +268,7 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
             cx<R> u[3][3];
             if (h < it.nh) nb = stage_hop<P>(it, h, a.p, d, u);
             s_nb[q] = nb;
-            if (nb >= 0) {
-#pragma unroll
-                for (int k = 0; k < 9; k++) {
-                    s_u[2 * k][q] = u[k / 3][k % 3].re;
-                    s_u[2 * k + 1][q] = u[k / 3][k % 3].im;
-                }
-            }
+            if (nb >= 0) put_link(s_u + q * LP, u);
         }
     }
     __syncthreads();
@@ -271,12 +290,11 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
             const int q = (D) * TS + sl;                                  \
             const int nb = s_nb[q];                                       \
             if (nb >= 0) {                                                \
-                R v[24];                                                  \
-                load_spinor<P>(a.in, tc.cb + nb, v);                      \
+                R v[24], f;                                               \
+                load_spinor_raw<P>(a.in, tc.cb + nb, v, &f);              \
                 cx<R> u[3][3];                                            \
-                _Pragma("unroll") for (int k = 0; k < 9; k++)             \
-                    u[k / 3][k % 3] = mk(s_u[2 * k][q], s_u[2 * k + 1][q]); \
-                hop_step<D>(v, u, acc);                                   \
+                get_link(s_u + q * LP, u);                                \
+                hop_step<D, P::NCH != 6>(v, u, acc, f);                   \
             }                                                             \
         }
         DDP_HOP_STEP(0)

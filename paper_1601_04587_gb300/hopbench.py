@@ -36,13 +36,13 @@ def main():
     import synth
 
     L = tuple(args.lattice)
-    U = synth.gauge_field(L, seed=synth.SEED_GAUGE)
+    U = synth.gauge_field_torch(L, seed=synth.SEED_GAUGE, device="cuda")
     ctx = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
     if args.tile_sites:
         ddp.ddp_set_param(ctx, "tile_sites", args.tile_sites)
     if args.tile_cols:
         ddp.ddp_set_param(ctx, "tile_cols", args.tile_cols)
-    gid = ddp.ddp_load_gauge(ctx, torch.from_numpy(U).cuda(), L, ddp.DDP_BC_ANTIPERIODIC)
+    gid = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
     did = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), L)
     ms, nbytes = ddp.ddp_time_hop(ctx, did, args.kappa, args.ncol, ddp.PRECISIONS[args.precision], args.iters)
     ddp.ddp_destroy(ctx)
