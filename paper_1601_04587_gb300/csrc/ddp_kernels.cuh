@@ -61,6 +61,12 @@ struct HopArgs {
     int skip;              // skip 2: leave columns whose outer solve has converged untouched
 };
 
+// Tiles are exactly HOP_TS = 32 sites (one warp per column of a tile); a
+// block holds at most HOP_MAX_CG = 12 columns.  The kernels use the tile size
+// as a compile-time constant.
+constexpr int HOP_TS = 32;
+constexpr int HOP_MAX_CG = 12;
+
 // Map a block/thread of a tile-structured launch to (item, column, site).
 struct TileCoord {
     int col, h, tile;
@@ -73,10 +79,10 @@ __device__ __forceinline__ TileCoord tile_coord(const Item &it, const Launch &L)
     int lb = blockIdx.x - it.blk0;
     t.tile = lb % it.ntiles;
     int cg = lb / it.ntiles;
-    int cl = threadIdx.x / L.TS;
-    int sl = threadIdx.x - cl * L.TS;
+    int cl = threadIdx.x / HOP_TS;
+    int sl = threadIdx.x - cl * HOP_TS;
     t.col = cg * L.CG + cl;
-    t.h = t.tile * L.TS + sl;
+    t.h = t.tile * HOP_TS + sl;
     t.valid = (t.col < it.ncol) && (t.h < it.nh) && (cl < L.CG);
     t.cb = it.fbase + (int64_t)t.col * it.nh;
     return t;
@@ -105,7 +111,7 @@ __device__ __forceinline__ void block_partials(const Item &it, const Launch &L, 
         s_nn[warp] = (double)nn;
     }
     __syncthreads();
-    int wpc = L.TS >> 5;  // warps per column
+    constexpr int wpc = HOP_TS >> 5;  // warps per column
     if ((int)threadIdx.x < L.CG) {
         int cl = threadIdx.x;
         int lb = (blk < 0 ? (int)blockIdx.x : blk) - it.blk0;
@@ -232,10 +238,6 @@ __device__ __forceinline__ void get_link(const R *d, cx<R> u[3][3]) {
     }
 }
 
-// Tiles are exactly HOP_TS = 32 sites (one warp per column of a tile); a
-// block holds at most HOP_MAX_CG = 12 columns.
-constexpr int HOP_TS = 32;
-constexpr int HOP_MAX_CG = 12;
 
 template <class P, int EPI, int DOT>
 __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_hop(HopArgs a) {
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
     __shared__ int s_nb[8 * TSMAX];
     __shared__ __align__(16) R s_u[8 * TSMAX * LP];
     load_item(a.L, it);
-    const int TS = a.L.TS;
+    constexpr int TS = HOP_TS;
     if (a.skip) {
         // a block whose columns are all finished has nothing to stage or compute
         const int cg = (blockIdx.x - it.blk0) / it.ntiles;
