@@ -21,8 +21,6 @@ __device__ __forceinline__ Cplx cadd(Cplx a, Cplx b) { return {a.re + b.re, a.im
 __device__ __forceinline__ Cplx csub(Cplx a, Cplx b) { return {a.re - b.re, a.im - b.im}; }
 __device__ __forceinline__ Cplx cmulc(Cplx a, Cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 __device__ __forceinline__ Cplx cscale(double s, Cplx a) { return {s * a.re, s * a.im}; }
-__device__ __forceinline__ Cplx timesi(Cplx a) { return {-a.im, a.re}; }
-__device__ __forceinline__ Cplx timesmi(Cplx a) { return {a.im, -a.re}; }
 
 struct ContractArgs {
     Item it;
@@ -39,102 +37,13 @@ __device__ __forceinline__ Cplx ld(const double2 *p) {
     return {v.x, v.y};
 }
 
-// M[rho][sigma] = S(y,x)_{rho a, sigma b} for colours (a, b) from the site's 144 entries in smem.
-__device__ __forceinline__ void spin_block(const Cplx *site, int a, int b, Cplx M[4][4]) {
-#pragma unroll
-    for (int r = 0; r < 4; r++)
-#pragma unroll
-        for (int s = 0; s < 4; s++) M[r][s] = site[(3 * s + b) * 12 + 3 * r + a];
-}
-
-// (C g5) M : rows permuted with phases
-__device__ __forceinline__ void cg5_left(const Cplx M[4][4], Cplx O[4][4]) {
-#pragma unroll
-    for (int s = 0; s < 4; s++) {
-        O[0][s] = timesmi(M[1][s]);
-        O[1][s] = timesi(M[0][s]);
-        O[2][s] = timesmi(M[3][s]);
-        O[3][s] = timesi(M[2][s]);
-    }
-}
-// M (C g5)
-__device__ __forceinline__ void cg5_right(const Cplx M[4][4], Cplx O[4][4]) {
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-        O[r][0] = timesi(M[r][1]);
-        O[r][1] = timesmi(M[r][0]);
-        O[r][2] = timesi(M[r][3]);
-        O[r][3] = timesmi(M[r][2]);
-    }
-}
-// M P-  (P- = 1/2 [[1,-1],[-1,1]] in 2x2 blocks)
-__device__ __forceinline__ void pminus_right(const Cplx M[4][4], Cplx O[4][4]) {
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-        Cplx d0 = cscale(0.5, csub(M[r][0], M[r][2]));
-        Cplx d1 = cscale(0.5, csub(M[r][1], M[r][3]));
-        O[r][0] = d0;
-        O[r][1] = d1;
-        O[r][2] = {-d0.re, -d0.im};
-        O[r][3] = {-d1.re, -d1.im};
-    }
-}
-
 __constant__ int kPerm[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {2, 1, 0}, {1, 0, 2}};
 __constant__ double kSign[6] = {1, 1, 1, -1, -1, -1};
 
-// W_N1 - W_N2 at one sink site with u = d = S:
+// Nucleon W_N1 - W_N2 at one sink site with u = d = S:
 //   W_N1 = eps^{abc} eps^{feg} tr[S^{ag T} C g5 S^{bf} C g5] tr[S^{ce} P-]
-//   W_N2 = eps^{abc} eps^{feg} tr[S^{ag T} C g5 S^{be} P- S^{cf} C g5]
-__device__ Cplx nucleon_site(const Cplx *site) {
-    Cplx w1 = {0, 0}, w2 = {0, 0};
-    for (int p1 = 0; p1 < 6; p1++) {
-        int a = kPerm[p1][0], b = kPerm[p1][1], c = kPerm[p1][2];
-        for (int p2 = 0; p2 < 6; p2++) {
-            int f = kPerm[p2][0], e = kPerm[p2][1], g = kPerm[p2][2];
-            double sg = kSign[p1] * kSign[p2];
-            Cplx Sag[4][4], M[4][4], X[4][4], Y[4][4], Z[4][4];
-            spin_block(site, a, g, Sag);
-            // W_N1: tr[Sag^T (C g5 Sbf C g5)] * tr[Sce P-]
-            spin_block(site, b, f, M);
-            cg5_left(M, X);
-            cg5_right(X, Y);
-            Cplx t1 = {0, 0};
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-#pragma unroll
-                for (int s = 0; s < 4; s++) t1 = cadd(t1, cmulc(Sag[r][s], Y[r][s]));
-            spin_block(site, c, e, M);
-            Cplx t2 = cscale(0.5, cadd(csub(M[0][0], M[0][2]), csub(M[1][1], M[1][3])));
-            t2 = cadd(t2, cscale(0.5, cadd(csub(M[2][2], M[2][0]), csub(M[3][3], M[3][1]))));
-            w1 = cadd(w1, cscale(sg, cmulc(t1, t2)));
-            // W_N2: tr[Sag^T (C g5 Sbe P-) (Scf C g5)]
-            spin_block(site, b, e, M);
-            cg5_left(M, X);
-            pminus_right(X, Y);
-            spin_block(site, c, f, M);
-            cg5_right(M, X);
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-#pragma unroll
-                for (int s = 0; s < 4; s++) {
-                    Cplx z = {0, 0};
-#pragma unroll
-                    for (int k = 0; k < 4; k++) z = cadd(z, cmulc(Y[r][k], X[k][s]));
-                    Z[r][s] = z;
-                }
-            Cplx t3 = {0, 0};
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-#pragma unroll
-                for (int s = 0; s < 4; s++) t3 = cadd(t3, cmulc(Sag[r][s], Z[r][s]));
-            w2 = cadd(w2, cscale(sg, t3));
-        }
-    }
-    return csub(w1, w2);
-}
-
-// Nucleon per sink site, one warp per site.  With Gamma = C g5, which maps
+//   W_N2 = eps^{abc} eps^{feg} tr[S^{ag T} C g5 S^{be} P- S^{cf} C g5].
+// With Gamma = C g5, which maps
 // spin rho to rho^1 with a phase, (Gamma M Gamma)_{rho sigma} = (-1)^(rho+sigma)
 // M_{rho^1, sigma^1}; with P- = (1 - g0)/2 of rank 2,
 //   (S^{be} P- S^{cf})_{alpha beta} = sum_{lambda=0,1} E_{alpha lambda} F_{lambda beta},
@@ -143,63 +52,88 @@ __device__ Cplx nucleon_site(const Cplx *site) {
 // so that with t_rho the row-rho parts of the traces,
 //   W_N1 = sum eps eps [sum_rho sum_sigma S^{ag}_{rho sigma} (-1)^(rho+sigma) S^{bf}_{rho^1 sigma^1}] tr[S^{ce} P-],
 //   W_N2 = sum eps eps  sum_rho sum_sigma S^{ag}_{rho sigma} (-1)^(rho+sigma) (E F)_{rho^1 sigma^1}.
-// The 36 epsilon pairs x 4 rows are spread over the 32 lanes.
 __device__ __forceinline__ Cplx sel(const Cplx *site, int rho, int a, int sigma, int b) {
     return site[(3 * sigma + b) * 12 + 3 * rho + a];  // S(y,x)_{rho a, sigma b}
 }
 
-__device__ Cplx nucleon_unit(const Cplx *site, int unit) {
+// grid (nchunk, e0), 128 threads: 4 warps x 8 sites = 32 sites of a time slice per block.
+// A warp takes its sites two at a time.  The factors that do not depend on the
+// row rho or on the whole epsilon pair are formed once per site in shared
+// memory: t2[c][e] = tr[S^{ce} P-], E[rho][b][e][lambda] and F[c][sigma][f][lambda]
+// above.  Then every lane evaluates 9 of the 2 x 144 (pair, rho) units as
+//   t1 = sum_sigma g S^{bf}_{rho^1 sigma^1},  X_lambda = sum_sigma g F[c][sigma^1][f][lambda],
+//   g = (-1)^(rho+sigma) S^{ag}_{rho sigma},
+//   unit = sign (t1 t2[c][e] - E[rho^1][b][e][0] X_0 - E[rho^1][b][e][1] X_1).
+constexpr int NUC_WARPS = 4, NUC_SITES_PER_WARP = 8;
+
+struct NucSite {
+    Cplx S[144];
+    Cplx t2[9];   // [c][e]
+    Cplx E[72];   // [rho][b][e][lambda]
+    Cplx F[72];   // [c][sigma][f][lambda]
+};
+
+__device__ __forceinline__ Cplx nucleon_unit(const NucSite &q, int unit) {
     const int pr = unit >> 2, rho = unit & 3;
     const int p1 = pr / 6, p2 = pr - 6 * (pr / 6);
     const int a = kPerm[p1][0], b = kPerm[p1][1], c = kPerm[p1][2];
     const int f = kPerm[p2][0], e = kPerm[p2][1], g = kPerm[p2][2];
     const double sg = kSign[p1] * kSign[p2];
     const int r1 = rho ^ 1;
-    // tr[S^{ce} P-]
-    Cplx t2 = {0, 0};
-#pragma unroll
-    for (int k = 0; k < 4; k++) t2 = cadd(t2, csub(sel(site, k, c, k, e), sel(site, k, c, k ^ 2, e)));
-    t2 = cscale(0.5, t2);
-    // E_{rho^1, lambda}, lambda = 0, 1
-    Cplx E0 = cscale(0.5, csub(sel(site, r1, b, 0, e), sel(site, r1, b, 2, e)));
-    Cplx E1 = cscale(0.5, csub(sel(site, r1, b, 1, e), sel(site, r1, b, 3, e)));
-    Cplx t1 = {0, 0}, t3 = {0, 0};
+    Cplx t1 = {0, 0}, x0 = {0, 0}, x1 = {0, 0};
 #pragma unroll
     for (int sigma = 0; sigma < 4; sigma++) {
         const int s1 = sigma ^ 1;
         const double ph = ((rho + sigma) & 1) ? -1.0 : 1.0;
-        Cplx sag = cscale(ph, sel(site, rho, a, sigma, g));
-        t1 = cadd(t1, cmulc(sag, sel(site, r1, b, s1, f)));
-        Cplx F0 = csub(sel(site, 0, c, s1, f), sel(site, 2, c, s1, f));
-        Cplx F1 = csub(sel(site, 1, c, s1, f), sel(site, 3, c, s1, f));
-        t3 = cadd(t3, cmulc(sag, cadd(cmulc(E0, F0), cmulc(E1, F1))));
+        const Cplx sag = cscale(ph, sel(q.S, rho, a, sigma, g));
+        t1 = cadd(t1, cmulc(sag, sel(q.S, r1, b, s1, f)));
+        x0 = cadd(x0, cmulc(sag, q.F[((c * 4 + s1) * 3 + f) * 2 + 0]));
+        x1 = cadd(x1, cmulc(sag, q.F[((c * 4 + s1) * 3 + f) * 2 + 1]));
     }
-    return cscale(sg, csub(cmulc(t1, t2), t3));
+    const Cplx t3 = cadd(cmulc(q.E[((r1 * 3 + b) * 3 + e) * 2 + 0], x0), cmulc(q.E[((r1 * 3 + b) * 3 + e) * 2 + 1], x1));
+    return cscale(sg, csub(cmulc(t1, q.t2[c * 3 + e]), t3));
 }
 
-// grid (nchunk, e0), 128 threads: 4 warps x 8 sites = 32 sites of a time slice per block.
-constexpr int NUC_WARPS = 4, NUC_SITES_PER_WARP = 8;
+// t2, E and F of a site from its 144 entries (item k of the 153 per site).
+__device__ __forceinline__ void nucleon_factor(NucSite &q, int k) {
+    if (k < 9) {
+        const int c = k / 3, e = k - 3 * (k / 3);
+        Cplx t = {0, 0};
+#pragma unroll
+        for (int r = 0; r < 4; r++) t = cadd(t, csub(sel(q.S, r, c, r, e), sel(q.S, r, c, r ^ 2, e)));
+        q.t2[k] = cscale(0.5, t);
+    } else if (k < 81) {
+        const int m = k - 9, lam = m & 1, e = (m >> 1) % 3, b = ((m >> 1) / 3) % 3, rho = (m >> 1) / 9;
+        q.E[m] = cscale(0.5, csub(sel(q.S, rho, b, lam, e), sel(q.S, rho, b, lam + 2, e)));
+    } else {
+        const int m = k - 81, lam = m & 1, f = (m >> 1) % 3, sigma = ((m >> 1) / 3) % 4, c = (m >> 1) / 12;
+        q.F[m] = csub(sel(q.S, lam, c, sigma, f), sel(q.S, lam + 2, c, sigma, f));
+    }
+}
 
 __global__ void __launch_bounds__(128) k_contract_nucleon(ContractArgs a) {
-    __shared__ Cplx s_site[NUC_WARPS][144];
+    __shared__ NucSite s_q[NUC_WARPS][2];
     __shared__ double s_re[NUC_WARPS], s_im[NUC_WARPS];
     const Item &it = a.it;
     const int slice_n = it.e[1] * it.e[2] * it.e[3];
     const int n = 2 * it.nh;
     const int t = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = blockIdx.x * (NUC_WARPS * NUC_SITES_PER_WARP) + warp * NUC_SITES_PER_WARP;
     Cplx acc = {0, 0};
-    for (int j = 0; j < NUC_SITES_PER_WARP; j++) {
-        const int r = blockIdx.x * (NUC_WARPS * NUC_SITES_PER_WARP) + warp * NUC_SITES_PER_WARP + j;
-        if (r >= slice_n) break;
-        const int l = t * slice_n + r;
-        for (int q = lane; q < 144; q += 32) {
-            const int col = q / 12, k = q - 12 * (q / 12);
-            s_site[warp][q] = ld(a.S + ((int64_t)col * n + l) * 12 + k);
+    for (int j = 0; j < NUC_SITES_PER_WARP; j += 2) {
+        const int nsite = min(2, slice_n - (r0 + j));
+        if (nsite <= 0) break;
+        for (int q = lane; q < 144 * nsite; q += 32) {
+            const int s = q / 144, m = q - 144 * s;
+            const int col = m / 12, k = m - 12 * (m / 12);
+            s_q[warp][s].S[m] = ld(a.S + ((int64_t)col * n + t * slice_n + r0 + j + s) * 12 + k);
         }
         __syncwarp();
+        for (int k = lane; k < 153 * nsite; k += 32) nucleon_factor(s_q[warp][k / 153], k % 153);
+        __syncwarp();
         Cplx v = {0, 0};
-        for (int u = lane; u < 144; u += 32) v = cadd(v, nucleon_unit(s_site[warp], u));
+        for (int u = lane; u < 144 * nsite; u += 32) v = cadd(v, nucleon_unit(s_q[warp][u / 144], u % 144));
         acc = cadd(acc, v);
         __syncwarp();
     }
@@ -238,9 +172,8 @@ __device__ __forceinline__ void block_sum_to(double2 *dst, Cplx v) {
     }
 }
 
-// grid (nchunk, e0); one thread per site of the slice.
+// Pion and noise traces: grid (nchunk, e0), one thread per site of the slice.
 __global__ void k_contract_slice(ContractArgs a) {
-    extern __shared__ Cplx site_smem[];
     const Item &it = a.it;
     int slice_n = it.e[1] * it.e[2] * it.e[3];
     int n = 2 * it.nh;
@@ -249,14 +182,7 @@ __global__ void k_contract_slice(ContractArgs a) {
     bool ok = r < slice_n;
     int l = t * slice_n + (ok ? r : 0);
     Cplx v = {0, 0};
-    if (a.kind == DDP_CONTRACT_NUCLEON) {
-        Cplx *site = site_smem + threadIdx.x * 144;
-        if (ok) {
-            for (int c = 0; c < 12; c++)
-                for (int j = 0; j < 12; j++) site[c * 12 + j] = ld(a.S + ((int64_t)c * n + l) * 12 + j);
-            v = nucleon_site(site);
-        }
-    } else if (ok) {
+    if (ok) {
         for (int c = 0; c < a.ncol; c++) {
             const double2 *ps = a.S + ((int64_t)c * n + l) * 12;
             if (a.kind == DDP_CONTRACT_PION) {
