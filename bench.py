@@ -185,6 +185,27 @@ class Workload:
         return h, h2d, d2h
 
 
+def pinned_link_rate(torch, bufs):
+    """Host<->device copy rates (GB/s) over the step's pinned host buffers, taken
+    just before the end-to-end timing: the host->device rate of this shared
+    link varies from run to run (the device->host rate much less), and the
+    end-to-end figure moves with it."""
+    nbytes = sum(b.numel() * b.element_size() for b in bufs)
+    devs = [torch.empty_like(b, device="cuda") for b in bufs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d, b in zip(devs, bufs):
+        d.copy_(b, non_blocking=True)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for d, b in zip(devs, bufs):
+        b.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del devs
+    return {"h2d": round(nbytes / (t1 - t0) / 1e9, 1), "d2h": round(nbytes / (t2 - t1) / 1e9, 1)}
+
+
 def timed(torch, fn, steps, dist=None):
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
@@ -260,6 +281,7 @@ def run_gpu(args):
     # end to end: host buffers through the C ABI, transfers inside the timed region
     host, h2d, d2h = wl.host_buffers()
     wl.step(host)
+    link = pinned_link_rate(torch, [host["U"]] + host["S"] + host["T"])
     e2e_secs = timed(torch, lambda: wl.step(host), max(1, args.steps // 2), dist)
     if dist:
         t = torch.tensor([e2e_secs], device="cuda")
@@ -303,7 +325,8 @@ def run_gpu(args):
                    if prec else "fp64",
                    "l2": "inputs larger than L2 (links 0.38 GB FP64, propagators 3.1 GB)",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "pinned_GBps": link},
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
