@@ -316,6 +316,59 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
 
 // ------------------------------------------------------------ vector updates
 
+// The reals of one storage chunk of an unscaled format, and back.
+template <class P>
+__device__ __forceinline__ void chunk_to_reals(const typename P::chunk &c, typename P::real *v);
+template <>
+__device__ __forceinline__ void chunk_to_reals<PF64>(const double2 &c, double *v) {
+    v[0] = c.x;
+    v[1] = c.y;
+}
+template <>
+__device__ __forceinline__ void chunk_to_reals<PF32>(const float4 &c, float *v) {
+    v[0] = c.x;
+    v[1] = c.y;
+    v[2] = c.z;
+    v[3] = c.w;
+}
+template <>
+__device__ __forceinline__ void chunk_to_reals<PBF16>(const uint4 &c, float *v) {
+    const float2 a0 = b2f(c.x), a1 = b2f(c.y), a2 = b2f(c.z), a3 = b2f(c.w);
+    v[0] = a0.x;
+    v[1] = a0.y;
+    v[2] = a1.x;
+    v[3] = a1.y;
+    v[4] = a2.x;
+    v[5] = a2.y;
+    v[6] = a3.x;
+    v[7] = a3.y;
+}
+template <>
+__device__ __forceinline__ void chunk_to_reals<PF16>(const uint4 &, float *) {}  // scaled: not chunk-local
+template <class P>
+__device__ __forceinline__ typename P::chunk reals_to_chunk(const typename P::real *v);
+template <>
+__device__ __forceinline__ double2 reals_to_chunk<PF64>(const double *v) {
+    return make_double2(v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ float4 reals_to_chunk<PF32>(const float *v) {
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ uint4 reals_to_chunk<PBF16>(const float *v) {
+    uint4 c;
+    c.x = f2b(v[0], v[1]);
+    c.y = f2b(v[2], v[3]);
+    c.z = f2b(v[4], v[5]);
+    c.w = f2b(v[6], v[7]);
+    return c;
+}
+template <>
+__device__ __forceinline__ uint4 reals_to_chunk<PF16>(const float *) {
+    return make_uint4(0, 0, 0, 0);
+}
+
 enum BlasOp { OP_P_UPDATE = 0, OP_S_UPDATE = 1, OP_XR_UPDATE = 2, OP_INIT = 3, OP_NORM = 4 };
 
 struct BlasArgs {
@@ -362,6 +415,46 @@ __global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
                 r[2 * j + 1] -= ar * v[2 * j + 1] + ai * v[2 * j];
             }
             store_spinor<P>(a.s, i, r);
+        } else if (OP == OP_XR_UPDATE && !P::SCALED) {
+            // x += alpha p + omega s ; r = s - omega t ; dots -- one storage chunk at a
+            // time (the fields do not alias), so few registers and many loads in flight
+            using C = typename P::chunk;
+            constexpr int NR = 24 / P::NCH;
+            const C *__restrict__ cx_ = reinterpret_cast<const C *>(a.x.p);
+            const C *__restrict__ cp_ = reinterpret_cast<const C *>(a.p.p);
+            const C *__restrict__ cs_ = reinterpret_cast<const C *>(a.s.p);
+            const C *__restrict__ ct_ = reinterpret_cast<const C *>(a.t.p);
+            const C *__restrict__ crh = reinterpret_cast<const C *>(a.rh.p);
+            C *__restrict__ ox = reinterpret_cast<C *>(a.x.p);
+            C *__restrict__ orr = reinterpret_cast<C *>(a.r.p);
+            const R ar = (R)S.alpha.x, ai = (R)S.alpha.y, wr = (R)S.omega.x, wi = (R)S.omega.y;
+            R n2 = 0;
+#pragma unroll
+            for (int j = 0; j < P::NCH; j++) {
+                const int64_t o = j * a.x.stride + i;
+                R x[NR], p[NR], s[NR], t[NR], rh[NR];
+                chunk_to_reals<P>(__ldg(cx_ + o), x);
+                chunk_to_reals<P>(__ldg(cp_ + o), p);
+                chunk_to_reals<P>(__ldg(cs_ + o), s);
+                chunk_to_reals<P>(__ldg(ct_ + o), t);
+                chunk_to_reals<P>(__ldg(crh + o), rh);
+#pragma unroll
+                for (int k = 0; k < NR / 2; k++) {
+                    x[2 * k] += (ar * p[2 * k] - ai * p[2 * k + 1]) + (wr * s[2 * k] - wi * s[2 * k + 1]);
+                    x[2 * k + 1] += (ar * p[2 * k + 1] + ai * p[2 * k]) + (wr * s[2 * k + 1] + wi * s[2 * k]);
+                    s[2 * k] -= wr * t[2 * k] - wi * t[2 * k + 1];
+                    s[2 * k + 1] -= wr * t[2 * k + 1] + wi * t[2 * k];
+                }
+                ox[o] = reals_to_chunk<P>(x);
+                orr[o] = reals_to_chunk<P>(s);
+#pragma unroll
+                for (int k = 0; k < NR / 2; k++) {
+                    cre += rh[2 * k] * s[2 * k] + rh[2 * k + 1] * s[2 * k + 1];
+                    cim += rh[2 * k] * s[2 * k + 1] - rh[2 * k + 1] * s[2 * k];
+                    n2 += s[2 * k] * s[2 * k] + s[2 * k + 1] * s[2 * k + 1];
+                }
+            }
+            nn = n2;
         } else if (OP == OP_XR_UPDATE) {  // x += alpha p + omega s ; r = s - omega t ; dots
             R x[24], p[24], s[24], t[24];
             load_spinor<P>(a.x, i, x);
