@@ -246,7 +246,7 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value);
  * hop with fused epilogue and dot product) on a domain with ncol columns in
  * the given storage format, timed with CUDA events over `iters` launches on
  * the context's stream; bytes_per_launch receives the kernel's algorithmic
- * HBM bytes (input, operand, shadow residual and output half-spinors plus
+ * HBM bytes (input, operand, shadow residual and output spinors plus
  * the links touching the output sites). */
 int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters,
                  float *ms_per_launch, double *bytes_per_launch);
