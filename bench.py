@@ -408,8 +408,10 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 5; 1 for the two-level workload, whose steps take minutes)")
+    ap.add_argument("--warmup", type=int, default=None,
+                    help="untimed warm-up steps (default 3; 0 for the two-level workload)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--skip-fp64", action="store_true")
@@ -421,6 +423,11 @@ def main():
     ap.add_argument("--no-conditional", action="store_true",
                     help="run the inner loop as host-polled graph chunks (profilers see its kernels)")
     args = ap.parse_args()
+    long_steps = args.workload == "multilevel"
+    if args.steps is None:
+        args.steps = 1 if long_steps else 5
+    if args.warmup is None:
+        args.warmup = 0 if long_steps else 3
     if args.warmup < 3 and args.workload == "slabs":
         args.warmup = 3
     if args.impl == "reference":
