@@ -271,6 +271,44 @@ def test_contractions(ddp, ctx, field, box, src):
     assert _rel(Cn[0::2] + 1j * Cn[1::2], oracle.noise_trace(LAT, o, e, eta, psi)) < CORR_TOL
 
 
+def test_series_and_contractions_host_buffers(ddp, ctx, field):
+    """Host arguments (pinned torch tensors and plain numpy arrays) give the same bits
+    as device arguments in the series terms and every contraction: the library stages
+    host buffers itself, and the arithmetic is the same."""
+    U, gid = field
+    src = (7, 1, 2, 3)
+    small, big = ((6, 0, 0, 0), (4, 4, 4, 6)), ((5, 0, 0, 0), (6, 4, 4, 6))
+    ds = ddp.ddp_set_domain(ctx, gid, *small)
+    db = ddp.ddp_set_domain(ctx, gid, *big)
+    Ss, *_ = oracle.propagator(U, LAT, AP, *small, 0.124, src)
+    Sb, *_ = oracle.propagator(U, LAT, AP, *big, 0.124, src)
+    Td = torch.zeros(Sb.shape, dtype=torch.complex128, device="cuda")
+    ddp.ddp_series_terms(ctx, ds, torch.from_numpy(Ss).cuda(), db, torch.from_numpy(Sb).cuda(), Td, 12)
+    Tp = torch.zeros(Sb.shape, dtype=torch.complex128).pin_memory()
+    ddp.ddp_series_terms(ctx, ds, torch.from_numpy(Ss).pin_memory(), db, torch.from_numpy(Sb).pin_memory(), Tp, 12)
+    Tn = np.zeros(Sb.shape, dtype=np.complex128)
+    ddp.ddp_series_terms(ctx, ds, Ss, db, Sb, Tn, 12)
+    assert np.array_equal(Tp.numpy(), Td.cpu().numpy()) and np.array_equal(Tn, Td.cpu().numpy())
+
+    n = Sb.shape[1]
+    eta = synth.diluted_noise_columns(synth.noise_field(n, 9))
+    cases = [(ddp.DDP_CONTRACT_NUCLEON, {}), (ddp.DDP_CONTRACT_PION, {}),
+             (ddp.DDP_CONTRACT_PSEUDO_LOCAL, {"src": src})]
+    for kind, kw in cases:
+        want = np.zeros(2 * LAT[0])
+        ddp.ddp_contract(ctx, kind, db, torch.from_numpy(Sb).cuda(), want, **kw)
+        for S_host in (torch.from_numpy(Sb).pin_memory(), Sb):
+            got = np.zeros(2 * LAT[0])
+            ddp.ddp_contract(ctx, kind, db, S_host, got, **kw)
+            assert np.array_equal(got, want), kind
+    want = np.zeros(2 * LAT[0])
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_NOISE, db, torch.from_numpy(Sb).cuda(), want,
+                     eta=torch.from_numpy(eta).cuda(), ncol=12)
+    got = np.zeros(2 * LAT[0])
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_NOISE, db, Sb, got, eta=eta, ncol=12)
+    assert np.array_equal(got, want)
+
+
 def test_gauge_region_variant(ddp, ctx, field):
     """A variant gauge field (links of one region replaced) solves like a
     freshly loaded field with the same links."""
