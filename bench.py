@@ -179,8 +179,11 @@ class Workload:
         nb = lambda x: x.numel() * x.element_size()  # noqa: E731
         S = sum(nb(x) for x in h["S"])
         T = sum(nb(x) for x in h["T"])
-        # H2D: gauge field, both propagators of every series term, every contraction input
-        h2d = nb(h["U"]) + sum(nb(h["S"][i - 1]) + nb(h["S"][i]) for i in range(1, 4)) + 3 * S
+        # H2D: gauge field, both propagators of every series term, the propagator of the
+        # nucleon and of the pion contraction, and the source-site rows (12 columns x 12
+        # complex) the local trace reads
+        h2d = (nb(h["U"]) + sum(nb(h["S"][i - 1]) + nb(h["S"][i]) for i in range(1, 4)) + 2 * S
+               + len(h["S"]) * 12 * 12 * 16)
         d2h = S + T + nb(h["C"]) + nb(h["tr"])
         return h, h2d, d2h
 

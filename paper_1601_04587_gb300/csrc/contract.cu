@@ -309,20 +309,7 @@ extern "C" int ddp_contract(ddp_ctx *ctx, int kind, int domain_id, const double 
     int nchunk = (slice_n + threads - 1) / threads;
     cudaError_t e = cudaSuccess;
     do {
-        if (!dev_ptr(S)) {
-            if ((e = cudaMallocAsync(&dS, sbytes, st)) != cudaSuccess) break;
-            ownS = true;
-            if ((e = cudaMemcpyAsync(dS, S, sbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
-        }
-        if (kind == DDP_CONTRACT_PSEUDO_NOISE && !dev_ptr(eta)) {
-            if ((e = cudaMallocAsync(&dE, sbytes, st)) != cudaSuccess) break;
-            ownE = true;
-            if ((e = cudaMemcpyAsync(dE, eta, sbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
-        }
-        if (outdev)
-            dOut = C_out;
-        else if ((e = cudaMallocAsync(&dOut, nout * sizeof(double2), st)) != cudaSuccess)
-            break;
+        int l_src = 0;
         if (kind == DDP_CONTRACT_PSEUDO_LOCAL) {
             if (!src) {
                 rc = DDP_ERR_INVALID_ARG;
@@ -339,8 +326,35 @@ extern "C" int ddp_contract(ddp_ctx *ctx, int kind, int domain_id, const double 
                 rc = DDP_ERR_INVALID_ARG;
                 break;
             }
-            int l = ((k[0] * d.e[1] + k[1]) * d.e[2] + k[2]) * d.e[3] + k[3];
-            k_local_trace<<<1, 1, 0, st>>>((const double2 *)dS, d.n, l, (double2 *)dOut);
+            l_src = ((k[0] * d.e[1] + k[1]) * d.e[2] + k[2]) * d.e[3] + k[3];
+        }
+        // the local trace reads one site of every column: from host memory only
+        // those 12 rows of 12 complex numbers are copied, not the whole propagator
+        const bool rows_only = kind == DDP_CONTRACT_PSEUDO_LOCAL && !dev_ptr(S);
+        if (rows_only) {
+            const size_t row = 12 * sizeof(double2);
+            if ((e = cudaMallocAsync(&dS, (size_t)ncol * row, st)) != cudaSuccess) break;
+            ownS = true;
+            if ((e = cudaMemcpy2DAsync(dS, row, reinterpret_cast<const double2 *>(S) + (size_t)l_src * 12,
+                                       (size_t)d.n * row, row, ncol, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                break;
+        } else if (!dev_ptr(S)) {
+            if ((e = cudaMallocAsync(&dS, sbytes, st)) != cudaSuccess) break;
+            ownS = true;
+            if ((e = cudaMemcpyAsync(dS, S, sbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        }
+        if (kind == DDP_CONTRACT_PSEUDO_NOISE && !dev_ptr(eta)) {
+            if ((e = cudaMallocAsync(&dE, sbytes, st)) != cudaSuccess) break;
+            ownE = true;
+            if ((e = cudaMemcpyAsync(dE, eta, sbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        }
+        if (outdev)
+            dOut = C_out;
+        else if ((e = cudaMallocAsync(&dOut, nout * sizeof(double2), st)) != cudaSuccess)
+            break;
+        if (kind == DDP_CONTRACT_PSEUDO_LOCAL) {
+            k_local_trace<<<1, 1, 0, st>>>((const double2 *)dS, rows_only ? 1 : d.n, rows_only ? 0 : l_src,
+                                           (double2 *)dOut);
             ctx->launches++;
         } else {
             if ((e = cudaMallocAsync(&dPart, (size_t)d.e[0] * nchunk * sizeof(double2), st)) != cudaSuccess) break;
