@@ -268,9 +268,8 @@ int ddp_serve_reset(ddp_ctx *ctx);
  * The paper has no counterpart: this entry point exists for callers that
  * must not allocate device memory, for instance code running under another
  * runtime's memory manager (a framework's custom operator whose allocator
- * owns the device), code that enqueues work while a CUDA graph is being
- * captured, or latency-critical loops where cudaMalloc/cudaFree would
- * synchronise the device.  It computes exactly what ddp_contract computes
+ * owns the device), or latency-critical loops where cudaMalloc/cudaFree
+ * would synchronise the device.  It computes exactly what ddp_contract computes
  * (same kernels, same reduction order) without a context and without
  * allocating: the per-time-slice partial sums go to one fixed device array
  * of DDP_STATIC_PARTIALS_MAX double2 entries (2 MiB) that lives in the

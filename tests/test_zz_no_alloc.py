@@ -2,9 +2,8 @@
 
 Some callers cannot allocate device memory at the moment they need a
 correlator: a custom operator inside another framework whose allocator owns
-the GPU, code that is enqueuing work while a CUDA graph is being captured, or a
-tight loop that cannot afford the device synchronisation cudaMalloc/cudaFree
-can cause.  ddp_contract_static serves them: it takes device buffers only and
+the GPU, or a tight loop that cannot afford the device synchronisation
+cudaMalloc/cudaFree can cause.  ddp_contract_static serves them: it takes device buffers only and
 keeps its partial sums in one fixed array inside the library.  These tests call
 it through the C ABI and check it against the allocating ddp_contract, twice
 in a row, because the fixed array keeps the previous call's contents.
