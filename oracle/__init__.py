@@ -112,6 +112,19 @@ def apply_hop(U, L, bc, origin, extent, psi):
     return out
 
 
+def hop_power(U, L, bc, origin, extent, kappa, p, psi):
+    """(kappa D_hop)^p psi on the box: p applications of the Dirichlet-restricted
+    hopping term (Sec. 2), each scaled by kappa, with 2 kappa D = 1 - kappa D_hop
+    (Sec. 5).  With psi = D^-1 g5 eta and p = 8 it is the vector contracted with
+    eta in the expanded stochastic trace of Eq. HPEtr."""
+    if p < 0:
+        raise ValueError("p must be >= 0")
+    v = _c(psi)
+    for _ in range(p):
+        v = kappa * apply_hop(U, L, bc, origin, extent, v)
+    return v
+
+
 def apply_dirac(U, L, bc, origin, extent, kappa, psi):
     """D_Gamma psi on the box; psi has shape (ncol, n, 4, 3) or (n, 4, 3)."""
     U = _c(U)

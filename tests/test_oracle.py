@@ -267,6 +267,35 @@ def test_hopping_expansion_trace_structure(field44):
                 assert abs(tr) > 1e-6
 
 
+def test_hopping_expansion_trace_identity(field44):
+    """Eq. HPEtr site by site: tr[g5 D^-1](x,x) = tr[g5 (kappa D_hop)^p D^-1](x,x) for
+    p <= 8, with D^-1 the dense inverse of D[Gamma, Gamma] built from the covariant
+    derivatives (independent of the oracle's hopping code), in a Dirichlet box with an
+    antiperiodic wrapped time direction; p = 9 breaks it."""
+    L, U = field44
+    kappa = 0.124
+    o, e = (0, 1, 0, 0), (4, 2, 2, 4)
+    n = int(np.prod(e))
+    DG = dense.restricted(dense.dirac_matrix(U, L, AP, kappa), L, o, e)
+    Dinv = np.linalg.inv(DG)
+    cols = np.ascontiguousarray(Dinv.T.reshape(12 * n, n, 4, 3))   # column j of D^-1 as a field
+    g5 = np.kron(oracle.gamma()[4], np.eye(3))
+
+    def site_traces(M):
+        return np.array([np.trace(g5 @ M[12 * s:12 * s + 12, 12 * s:12 * s + 12]) for s in range(n)])
+
+    want = site_traces(Dinv)
+    for p in (4, 8, 9):
+        hp = oracle.hop_power(U, L, AP, o, e, kappa, p, cols)        # [j] = (k D_hop)^p D^-1 e_j
+        M = hp.reshape(12 * n, 12 * n).T
+        got = site_traces(M)
+        err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+        if p <= 8:
+            assert err < 1e-10, (p, err)   # rounding of the dense inverse; a wrong power of kappa is O(1)
+        else:
+            assert err > 1e-6, (p, err)
+
+
 def test_telescoping_series(field44):
     """S^(0) + sum_i [S^(i) - S^(i-1)] = S on the full lattice (Eq. Dseries)."""
     L, U = field44
