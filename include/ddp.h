@@ -141,6 +141,21 @@ int ddp_domain_sites(ddp_ctx *ctx, int domain_id, int64_t *n_sites, int64_t *glo
 int ddp_apply_dirac(ddp_ctx *ctx, int domain_id, double kappa, const double *psi, double *out, int ncol,
                     int precision);
 
+/* out = (kappa D_hop)^p psi on the domain, in FP64: p applications of the
+ * hopping term of D_Gamma (the Dirichlet-masked stencil of Sec. 2, with
+ * 2 kappa D = 1 - kappa D_hop of Sec. 5), each scaled by kappa.  This is the
+ * operator of the hopping-parameter-expanded trace, Eq. HPEtr:
+ * tr{g5 D^-1} = kappa^p tr{g5 D_hop^p D^-1} for p <= 8.  With
+ * psi = D_Gamma^-1 g5 eta (ddp_solve_sources) and p = 8,
+ * ddp_contract(DDP_CONTRACT_PSEUDO_NOISE, out, eta = g5 eta) is the expanded
+ * stochastic estimator of sum_x tr{g5 D^-1(x,x)} per time slice, because
+ * (g5 eta)^+ g5 v = eta^+ v.
+ * psi, out: [ncol][n_sites][4][3] complex, domain-local lexicographic order,
+ * host or device memory (may not alias).  p = 0 copies psi.
+ * DDP_ERR_INVALID_ARG for kappa <= 0, p < 0, p > 64 or ncol < 1;
+ * DDP_ERR_NOT_FOUND for an unknown domain.  Returns when out is complete. */
+int ddp_hop_power(ddp_ctx *ctx, int domain_id, double kappa, int p, const double *psi, double *out, int ncol);
+
 /* Domain propagator S^(i)(y,x) = D_Gamma^{-1}(y,x) (Eq. diric) for the 12
  * spin-colour point sources at global site src (which must lie in the
  * domain).  Stops when every column has |eta - D_Gamma psi|_2 / |eta|_2 <= tol

@@ -74,6 +74,7 @@ def lib():
             "ddp_free_domain": ([vp, i], i),
             "ddp_domain_sites": ([vp, i, ctypes.POINTER(ctypes.c_int64), vp, vp], i),
             "ddp_apply_dirac": ([vp, i, d, vp, vp, i, i], i),
+            "ddp_hop_power": ([vp, i, d, i, vp, vp, i], i),
             "ddp_solve_propagator": ([vp, i, d, d, i4, d, i, vp, ctypes.POINTER(ddp_solve_info)], i),
             "ddp_solve_sources": ([vp, i, d, d, vp, i, d, i, vp, ctypes.POINTER(ddp_solve_info)], i),
             "ddp_solve_batch": ([vp, ctypes.POINTER(ddp_solve_req), i, i, ctypes.POINTER(ddp_solve_info)], i),
@@ -191,6 +192,11 @@ def ddp_domain_sites(ctx, domain_id, global_index_out=None, eo_index_out=None) -
 def ddp_apply_dirac(ctx, domain_id, kappa, psi, out, ncol, precision=DDP_PREC_FP64):
     return _check(ctx, lib().ddp_apply_dirac(ctx, int(domain_id), float(kappa), _ptr(psi), _ptr(out), int(ncol),
                                              int(precision)), "ddp_apply_dirac")
+
+
+def ddp_hop_power(ctx, domain_id, kappa, p, psi, out, ncol=12):
+    return _check(ctx, lib().ddp_hop_power(ctx, int(domain_id), float(kappa), int(p), _ptr(psi), _ptr(out), int(ncol)),
+                  "ddp_hop_power")
 
 
 def ddp_solve_propagator(ctx, domain_id, kappa, csw, src, tol, precision, S_out, raise_on_fail=False):

@@ -109,6 +109,8 @@ int solve_jobs_dispatch(ddp_ctx *ctx, int prec, std::vector<Job> &jobs, std::vec
 template <class P>
 int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *out, int prec);
 template <class P>
+int hop_power_impl(ddp_ctx *ctx, const Job &job, int p, const double *psi, double *out);
+template <class P>
 int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, double *bytes);
 
 }  // namespace ddp
@@ -663,6 +665,32 @@ int ddp_apply_dirac(ddp_ctx *ctx, int domain_id, double kappa, const double *psi
         default: rc = apply_dirac_impl<PBF16>(ctx, j, (const double *)si.dev, (double *)so.dev, precision); break;
     }
     if (rc) return rc;
+    if ((rc = so.copy_out())) return rc;
+    DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return DDP_OK;
+}
+
+// (kappa D_hop)^p psi on a domain, FP64 (Eq. HPEtr, Sec. 2 restriction).
+int ddp_hop_power(ddp_ctx *ctx, int domain_id, double kappa, int p, const double *psi, double *out, int ncol) {
+    if (!ctx || !psi || !out || ncol < 1 || !(kappa > 0) || p < 0 || p > 64) return DDP_ERR_INVALID_ARG;
+    const DomainDev *d;
+    const GaugeDev *g;
+    int rc = find_domain(ctx, domain_id, &d, &g);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    StreamJoin sj(ctx);
+    size_t bytes = (size_t)ncol * d->n * 12 * sizeof(double2);
+    Staged si, so;
+    if ((rc = si.init(ctx, psi, bytes, true))) return rc;
+    if ((rc = so.init(ctx, out, bytes, false))) return rc;
+    Job j;
+    memset(&j, 0, sizeof(j));
+    j.g = g;
+    memcpy(j.o, d->o, sizeof(j.o));
+    memcpy(j.e, d->e, sizeof(j.e));
+    j.kappa = kappa;
+    j.ncol = ncol;
+    if ((rc = hop_power_impl<PF64>(ctx, j, p, (const double *)si.dev, (double *)so.dev))) return rc;
     if ((rc = so.copy_out())) return rc;
     DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return DDP_OK;

@@ -15,6 +15,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 
@@ -462,6 +463,75 @@ int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *ou
     launch_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
     k_unpack_low<P><<<nb, 256, 0, st>>>(pa, oe, oo);
     ctx->launches += 4;
+    DDP_CUDA(ctx, cudaGetLastError());
+    return DDP_OK;
+}
+
+// out *= s over n complex numbers.
+static __global__ void k_scale_complex(double2 *out, int64_t n, double s) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_double2(s * out[i].x, s * out[i].y);
+}
+
+// out = (kappa D_hop)^p psi on a domain in FP64 (Eq. HPEtr with the
+// Dirichlet-restricted hopping term of Sec. 2): p pairs of plain hop launches
+// (odd -> even, even -> odd) between two even-odd field pairs, then kappa^p
+// applied once to the unpacked result.  psi and out: device pointers.
+template <class P>
+int hop_power_impl(ddp_ctx *ctx, const Job &job, int p, const double *psi, double *out) {
+    static_assert(P::IS64, "the hopping power is an FP64 operation");
+    std::vector<Job> jobs(1, job);
+    Plan plan;
+    make_plan(jobs, DDP_PREC_FP64, ctx->prm, plan);
+    const int64_t NF = plan.nfield;
+    size_t need = 4 * field_bytes<P>(NF) + sizeof(Item) + 1024;
+    DDP_CUDA(ctx, ctx->scratch.reserve(need));
+    Arena &a = ctx->scratch;
+    a.reset();
+    FieldView f[2][2] = {{carve_field<P>(a, NF), carve_field<P>(a, NF)}, {carve_field<P>(a, NF), carve_field<P>(a, NF)}};
+    Item *d_items = (Item *)a.take(sizeof(Item));
+    cudaStream_t st = ctx->stream;
+    DDP_CUDA(ctx, cudaMemcpyAsync(d_items, plan.items.data(), sizeof(Item), cudaMemcpyHostToDevice, st));
+    PackArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.it = plan.items[0];
+    pa.user = (const double2 *)psi;
+    pa.uout = (double2 *)out;
+    const int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
+    const unsigned nb = (unsigned)((nt + 255) / 256);
+    k_pack_low<P><<<nb, 256, 0, st>>>(pa, f[0][0], f[0][1]);
+    Launch L;
+    L.items = d_items;
+    L.nitems = 1;
+    L.TS = plan.TS;
+    L.CG = plan.CG;
+    FieldView none = {nullptr, nullptr, 0};
+    HopArgs h;
+    h.st = nullptr;
+    h.skip = 0;
+    h.L = L;
+    h.v1 = none;
+    h.v2 = none;
+    h.rh = none;
+    h.part.c = nullptr;
+    h.part.n = nullptr;
+    int cur = 0;
+    for (int k = 0; k < p; k++) {
+        const int nxt = cur ^ 1;
+        h.p = 0;
+        h.in = f[cur][1];
+        h.out = f[nxt][0];
+        launch_hop<P, EPI_PLAIN, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+        h.p = 1;
+        h.in = f[cur][0];
+        h.out = f[nxt][1];
+        launch_hop<P, EPI_PLAIN, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+        cur = nxt;
+    }
+    k_unpack_low<P><<<nb, 256, 0, st>>>(pa, f[cur][0], f[cur][1]);
+    const int64_t nc = (int64_t)pa.it.ncol * 2 * pa.it.nh * 12;
+    k_scale_complex<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>((double2 *)out, nc, std::pow(job.kappa, p));
+    ctx->launches += 3 + 2 * (long)p;
     DDP_CUDA(ctx, cudaGetLastError());
     return DDP_OK;
 }

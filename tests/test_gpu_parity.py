@@ -309,6 +309,52 @@ def test_series_and_contractions_host_buffers(ddp, ctx, field):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("box", BOXES[:4])
+def test_hop_power(ddp, ctx, field, box):
+    """(kappa D_hop)^p in FP64 against the oracle's p plain applications of the
+    restricted hopping term (Eq. HPEtr operator), p = 0, 1, 8; host arguments give
+    the same bits as device arguments."""
+    U, gid = field
+    o, e = box
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    rng = np.random.default_rng(3)
+    psi = rng.standard_normal((3, n, 4, 3)) + 1j * rng.standard_normal((3, n, 4, 3))
+    for p in (0, 1, 8):
+        want = oracle.hop_power(U, LAT, AP, o, e, 0.124, p, psi)
+        out = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda")
+        ddp.ddp_hop_power(ctx, did, 0.124, p, torch.from_numpy(psi).cuda(), out, 3)
+        got = out.cpu().numpy()
+        assert max(_col_errors(got, want)) < 1e-12, p
+        host = np.zeros_like(psi)
+        ddp.ddp_hop_power(ctx, did, 0.124, p, psi, host, 3)
+        assert np.array_equal(host, got)
+    for bad in ((-1, 0.124), (65, 0.124), (8, 0.0)):
+        with pytest.raises(ddp.DDPError) as ei:
+            ddp.ddp_hop_power(ctx, did, bad[1], bad[0], psi, np.zeros_like(psi), 3)
+        assert ei.value.status == ddp.DDP_ERR_INVALID_ARG
+
+
+def test_expanded_noise_trace(ddp, ctx, field):
+    """The stochastic trace of Eq. HPEtr with p = 8: psi = D^-1 g5 eta, then
+    (kappa D_hop)^8 psi contracted with g5 eta (= eta^+ [kappa^8 D_hop^8 D^-1 g5 eta]
+    per time slice), against the oracle's same steps."""
+    U, gid = field
+    o, e = BOXES[1]
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    eta = synth.diluted_noise_columns(synth.noise_field(n, 13))
+    g5eta = np.ascontiguousarray(np.einsum("ab,cnbk->cnak", oracle.gamma()[4], eta))
+    psi, *_ = oracle.solve(U, LAT, AP, o, e, 0.124, g5eta)
+    want = oracle.noise_trace(LAT, o, e, g5eta, oracle.hop_power(U, LAT, AP, o, e, 0.124, 8, psi))
+    v = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda")
+    ddp.ddp_hop_power(ctx, did, 0.124, 8, torch.from_numpy(psi).cuda(), v, 12)
+    C = torch.zeros(2 * LAT[0], dtype=torch.float64, device="cuda")
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_NOISE, did, v, C, eta=torch.from_numpy(g5eta).cuda(), ncol=12)
+    Cn = C.cpu().numpy()
+    assert _rel(Cn[0::2] + 1j * Cn[1::2], want) < CORR_TOL
+
+
 def test_gauge_region_variant(ddp, ctx, field):
     """A variant gauge field (links of one region replaced) solves like a
     freshly loaded field with the same links."""
