@@ -77,3 +77,23 @@ def restricted(D, L, origin, extent):
     """D_Gamma = D[Gamma, Gamma] (Eq. blkdec) as a dense array."""
     idx = box_component_index(L, origin, extent)
     return D[idx][:, idx].toarray()
+
+
+def boundary_source(U, L, bc, from_box, psi_from, to_box):
+    """sigma = -D[Gamma_to, Gamma_from minus Gamma_to] psi_from: the couplings of D (App. A)
+    from sites of the `from` box that lie outside the `to` box into the `to` box, i.e.
+    the off-diagonal blocks D_dGamma of Eq. blkdec that the Dirichlet boundary of the
+    `to` box drops.  With from = Gamma-bar_0, to = Gamma*_0 and psi = D^-1_{Gamma-bar_0} eta,
+    D^-1_{Gamma*_0} sigma is the factorized propagator of Eq. approxlong.
+    psi_from: (ncol, n_from, 4, 3); returns (ncol, n_to, 4, 3).  The hopping blocks
+    do not depend on kappa (any value builds them)."""
+    D = dirac_matrix(U, L, bc, 0.125)
+    idx_to = box_component_index(L, *to_box)
+    idx_from = box_component_index(L, *from_box)
+    to_sites = set((idx_to // 12).tolist())
+    keep = np.array([(i // 12) not in to_sites for i in idx_from])
+    psi = np.asarray(psi_from).reshape(psi_from.shape[0], -1)
+    B = D[idx_to][:, idx_from[keep]]
+    sigma = -(B @ psi[:, keep].T).T
+    n_to = len(idx_to) // 12
+    return np.ascontiguousarray(sigma.reshape(psi_from.shape[0], n_to, 4, 3))

@@ -296,6 +296,55 @@ def test_hopping_expansion_trace_identity(field44):
             assert err > 1e-6, (p, err)
 
 
+def test_boundary_source_block_row(field44):
+    """Row block Gamma_to of D S = eta (Eq. blkdec): D_{Gamma_to} S|to = eta|to + sigma with
+    sigma the dropped couplings from the rest of the lattice (from = whole lattice),
+    for a Dirichlet box and for a time slab wrapped across the antiperiodic boundary."""
+    L, U = field44
+    kappa = 0.124
+    src = (1, 2, 0, 3)
+    S, *_ = oracle.propagator(U, L, AP, (0, 0, 0, 0), L, kappa, src)
+    gi_full = oracle.domain_maps(L, (0, 0, 0, 0), L)[0]
+    for to in [((3, 0, 0, 0), (2, 4, 4, 4)), ((1, 1, 0, 2), (2, 3, 4, 2))]:
+        gi = oracle.domain_maps(L, *to)[0]
+        full = np.zeros((12, 256, 4, 3), dtype=np.complex128)
+        full[:, gi_full] = S
+        S_to = np.ascontiguousarray(full[:, gi])
+        sigma = dense.boundary_source(U, L, AP, ((0, 0, 0, 0), L), S, to)
+        eta_to = np.zeros_like(S_to)
+        try:                                        # the source, where it lies in the box
+            k = oracle.local_index(L, to[0], to[1], src)
+            for c in range(12):
+                eta_to[c, k, c // 3, c % 3] = 1
+        except ValueError:
+            pass
+        lhs = oracle.apply_dirac(U, L, AP, to[0], to[1], kappa, S_to)
+        assert _rel(lhs, eta_to + sigma) < 1e-10
+
+
+def test_factorized_propagator_exact_limit(field44):
+    """Eq. approxlong with Gamma-bar_0 = the whole lattice is exact: for a source outside
+    Gamma*_0, D^-1_{Gamma*_0} sigma(D^-1 eta) = S on Gamma*_0; with a thinner Gamma-bar_0
+    it is only an approximation (differs)."""
+    L, U = field44
+    kappa = 0.124
+    src = (0, 1, 2, 3)
+    star = ((2, 0, 0, 0), (2, 4, 4, 4))            # Gamma*_0: slices 2, 3
+    S, *_ = oracle.propagator(U, L, AP, (0, 0, 0, 0), L, kappa, src)
+    gi_full = oracle.domain_maps(L, (0, 0, 0, 0), L)[0]
+    gi = oracle.domain_maps(L, *star)[0]
+    full = np.zeros((12, 256, 4, 3), dtype=np.complex128)
+    full[:, gi_full] = S
+    sigma = dense.boundary_source(U, L, AP, ((0, 0, 0, 0), L), S, star)
+    Sf, *_ = oracle.solve(U, L, AP, *star, kappa, sigma)
+    assert _rel(Sf, full[:, gi]) < 1e-9
+    bar = ((0, 0, 0, 0), (3, 4, 4, 4))             # Gamma-bar_0: slices 0..2, overlapping Gamma*_0 by one
+    Sb, *_ = oracle.propagator(U, L, AP, *bar, kappa, src)
+    sigma_b = dense.boundary_source(U, L, AP, bar, Sb, star)
+    Sfb, *_ = oracle.solve(U, L, AP, *star, kappa, sigma_b)
+    assert _rel(Sfb, full[:, gi]) > 1e-6
+
+
 def test_telescoping_series(field44):
     """S^(0) + sum_i [S^(i) - S^(i-1)] = S on the full lattice (Eq. Dseries)."""
     L, U = field44
