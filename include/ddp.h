@@ -195,6 +195,19 @@ int ddp_solve_batch(ddp_ctx *ctx, const ddp_solve_req *reqs, int n, int precisio
 int ddp_series_terms(ddp_ctx *ctx, int domain_small, const double *S_small, int domain_big, const double *S_big,
                      double *T_out, int ncol);
 
+/* Boundary coupling of two domains of the same gauge field (Eq. blkdec):
+ * sigma = -D[to, from \ to] psi, the terms of D that connect sites of the
+ * `from` domain lying outside the `to` domain to sites of `to` -- exactly the
+ * hops the Dirichlet boundary of `to` drops, with the gauge field's time
+ * boundary condition.  With from = Gamma-bar_0, to = Gamma*_0 and
+ * psi = D^{-1}_{Gamma-bar_0} eta (ddp_solve_propagator / ddp_solve_sources),
+ * D^{-1}_{Gamma*_0} sigma (ddp_solve_sources) is the factorized propagator
+ * S^(f) = -D^{-1}_{Gamma*_0} D_{dGamma*_0} D^{-1}_{Gamma-bar_0} of Eq. approxlong.
+ * FP64.  psi [ncol][n_from][4][3], sigma [ncol][n_to][4][3] complex,
+ * domain-local lexicographic order, host or device memory.
+ * DDP_ERR_INVALID_ARG for ncol < 1 or domains of different gauge fields. */
+int ddp_boundary_source(ddp_ctx *ctx, int domain_from, const double *psi, int domain_to, double *sigma, int ncol);
+
 /* Wick contractions of a solved propagator on a domain.
  *  PSEUDO_LOCAL: S = 12 point-source columns, src = the source; C_out[2] = tr{g5 S(x,x)}.
  *  PSEUDO_NOISE: S = psi_c = D_Gamma^{-1} eta_c, eta = the ncol sources;

@@ -75,6 +75,7 @@ def lib():
             "ddp_domain_sites": ([vp, i, ctypes.POINTER(ctypes.c_int64), vp, vp], i),
             "ddp_apply_dirac": ([vp, i, d, vp, vp, i, i], i),
             "ddp_hop_power": ([vp, i, d, i, vp, vp, i], i),
+            "ddp_boundary_source": ([vp, i, vp, i, vp, i], i),
             "ddp_solve_propagator": ([vp, i, d, d, i4, d, i, vp, ctypes.POINTER(ddp_solve_info)], i),
             "ddp_solve_sources": ([vp, i, d, d, vp, i, d, i, vp, ctypes.POINTER(ddp_solve_info)], i),
             "ddp_solve_batch": ([vp, ctypes.POINTER(ddp_solve_req), i, i, ctypes.POINTER(ddp_solve_info)], i),
@@ -197,6 +198,11 @@ def ddp_apply_dirac(ctx, domain_id, kappa, psi, out, ncol, precision=DDP_PREC_FP
 def ddp_hop_power(ctx, domain_id, kappa, p, psi, out, ncol=12):
     return _check(ctx, lib().ddp_hop_power(ctx, int(domain_id), float(kappa), int(p), _ptr(psi), _ptr(out), int(ncol)),
                   "ddp_hop_power")
+
+
+def ddp_boundary_source(ctx, domain_from, psi, domain_to, sigma, ncol=12):
+    return _check(ctx, lib().ddp_boundary_source(ctx, int(domain_from), _ptr(psi), int(domain_to), _ptr(sigma),
+                                                 int(ncol)), "ddp_boundary_source")
 
 
 def ddp_solve_propagator(ctx, domain_id, kappa, csw, src, tol, precision, S_out, raise_on_fail=False):

@@ -312,6 +312,103 @@ __global__ void k_series(SeriesArgs a) {
     }
 }
 
+// sigma = -D[to, from minus to] psi (Eq. blkdec): for every site y of `to`, the hops
+// of D_hop that the Dirichlet boundary of `to` drops and that start at a site of
+// `from`; D = 1/(2 kappa) - D_hop / 2, so sigma = + D_hop[to, from minus to] psi / 2.
+struct BoundaryArgs {
+    Item to, from;
+    const double2 *psi;  // [ncol][n_from][12]
+    double2 *sigma;      // [ncol][n_to][12]
+    int ncol;
+};
+
+template <int D>
+__device__ __forceinline__ void boundary_hop(const BoundaryArgs &a, const int x[4], int px, int col,
+                                             cx<double> acc[4][3]) {
+    constexpr int MU = D >> 1;
+    constexpr bool FWD = !(D & 1);
+    const Item &t = a.to;
+    int w[4] = {x[0], x[1], x[2], x[3]};
+    double f = 1.0;
+    if (FWD) {
+        w[MU] = x[MU] + 1;
+        if (w[MU] == t.L[MU]) {
+            w[MU] = 0;
+            if (MU == 0 && t.bc == 2) return;
+            if (MU == 0 && t.bc == 1) f = -1.0;
+        }
+    } else {
+        w[MU] = x[MU] - 1;
+        if (w[MU] < 0) {
+            w[MU] = t.L[MU] - 1;
+            if (MU == 0 && t.bc == 2) return;
+            if (MU == 0 && t.bc == 1) f = -1.0;
+        }
+    }
+    int kt[4], kf[4];
+    bool in_to = true, in_from = true;
+    for (int m = 0; m < 4; m++) {
+        int dt = w[m] - t.o[m], df = w[m] - a.from.o[m];
+        if (dt < 0) dt += t.L[m];
+        if (df < 0) df += t.L[m];
+        kt[m] = dt;
+        kf[m] = df;
+        in_to = in_to && (dt < t.e[m]);
+        in_from = in_from && (df < a.from.e[m]);
+    }
+    if (in_to || !in_from) return;
+    const int64_t nf = 2 * (int64_t)a.from.nh;
+    const double2 *ps = a.psi + ((int64_t)col * nf + local_lex(a.from, kf)) * 12;
+    double v[24];
+    for (int j = 0; j < 12; j++) {
+        const double2 c = ps[j];
+        v[2 * j] = c.x;
+        v[2 * j + 1] = c.y;
+    }
+    cx<double> u[3][3];
+    if (FWD) {
+        load_link<PF64>(t.links64, t.gV, MU, link_row(t, x, px), u);
+    } else {
+        cx<double> b[3][3];
+        load_link<PF64>(t.links64, t.gV, MU, link_row(t, w, px ^ 1), b);
+        for (int i = 0; i < 3; i++)
+            for (int k = 0; k < 3; k++) u[i][k] = conj(b[k][i]);
+    }
+    for (int i = 0; i < 3; i++)
+        for (int k = 0; k < 3; k++) u[i][k] = f * u[i][k];
+    hop_step<D, true>(v, u, acc, 1.0);
+}
+
+__global__ void k_boundary_source(BoundaryArgs a) {
+    const int64_t nt = 2 * (int64_t)a.to.nh;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nt * a.ncol) return;
+    const int col = (int)(g / nt);
+    const int l = (int)(g - col * nt);
+    int k[4], x[4];
+    local_coords(a.to, l, k);
+    int px = 0;
+    for (int m = 0; m < 4; m++) {
+        x[m] = (a.to.o[m] + k[m]) % a.to.L[m];
+        px += x[m];
+    }
+    px &= 1;
+    cx<double> acc[4][3];
+    for (int s2 = 0; s2 < 4; s2++)
+        for (int c = 0; c < 3; c++) acc[s2][c] = mk(0.0, 0.0);
+    boundary_hop<0>(a, x, px, col, acc);
+    boundary_hop<1>(a, x, px, col, acc);
+    boundary_hop<2>(a, x, px, col, acc);
+    boundary_hop<3>(a, x, px, col, acc);
+    boundary_hop<4>(a, x, px, col, acc);
+    boundary_hop<5>(a, x, px, col, acc);
+    boundary_hop<6>(a, x, px, col, acc);
+    boundary_hop<7>(a, x, px, col, acc);
+    double2 *out = a.sigma + ((int64_t)col * nt + l) * 12;
+    for (int s2 = 0; s2 < 4; s2++)
+        for (int c = 0; c < 3; c++) out[3 * s2 + c] = make_double2(0.5 * acc[s2][c].re, 0.5 * acc[s2][c].im);
+}
+
 int check_box(const GaugeDev &g, const int o[4], const int e[4]) {
     for (int m = 0; m < 4; m++)
         if (e[m] < 1 || e[m] > g.L[m]) return DDP_ERR_INVALID_ARG;
@@ -865,6 +962,36 @@ int ddp_series_terms(ddp_ctx *ctx, int domain_small, const double *S_small, int 
     ctx->launches++;
     DDP_CUDA(ctx, cudaGetLastError());
     if ((rc = t.copy_out())) return rc;
+    DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return DDP_OK;
+}
+
+// Boundary coupling of two domains of one gauge field (Eq. blkdec), the source of
+// the second solve of the factorized propagator (Eq. approxlong).
+int ddp_boundary_source(ddp_ctx *ctx, int domain_from, const double *psi, int domain_to, double *sigma, int ncol) {
+    if (!ctx || !psi || !sigma || ncol < 1) return DDP_ERR_INVALID_ARG;
+    const DomainDev *df, *dt;
+    const GaugeDev *gf, *gt;
+    int rc = find_domain(ctx, domain_from, &df, &gf);
+    if (rc) return rc;
+    if ((rc = find_domain(ctx, domain_to, &dt, &gt))) return rc;
+    if (gf != gt) return DDP_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    StreamJoin sj(ctx);
+    Staged a, b;
+    if ((rc = a.init(ctx, psi, (size_t)ncol * df->n * 12 * sizeof(double2), true))) return rc;
+    if ((rc = b.init(ctx, sigma, (size_t)ncol * dt->n * 12 * sizeof(double2), false))) return rc;
+    BoundaryArgs ba;
+    ba.to = item_of(*gt, *dt, ncol, DDP_PREC_FP64);
+    ba.from = item_of(*gf, *df, ncol, DDP_PREC_FP64);
+    ba.psi = (const double2 *)a.dev;
+    ba.sigma = (double2 *)b.dev;
+    ba.ncol = ncol;
+    const int64_t nt = (int64_t)ncol * dt->n;
+    k_boundary_source<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(ba);
+    ctx->launches++;
+    DDP_CUDA(ctx, cudaGetLastError());
+    if ((rc = b.copy_out())) return rc;
     DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return DDP_OK;
 }

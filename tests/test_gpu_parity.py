@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import dense
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -353,6 +354,62 @@ def test_expanded_noise_trace(ddp, ctx, field):
     ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_NOISE, did, v, C, eta=torch.from_numpy(g5eta).cuda(), ncol=12)
     Cn = C.cpu().numpy()
     assert _rel(Cn[0::2] + 1j * Cn[1::2], want) < CORR_TOL
+
+
+GB0 = ((0, 0, 0, 0), (4, 4, 4, 6))      # Gamma-bar_0: time slices 0..3
+GS0 = ((3, 0, 0, 0), (5, 4, 4, 6))      # Gamma*_0: slices 3..7, overlapping Gamma-bar_0 by one slice
+
+
+@pytest.mark.parametrize("pair", [(GB0, GS0),
+                                  (((0, 0, 0, 0), LAT), ((5, 1, 3, 2), (3, 2, 3, 4))),
+                                  (((0, 0, 0, 0), (8, 4, 2, 6)), ((0, 0, 2, 0), (8, 4, 2, 6)))])
+def test_boundary_source(ddp, ctx, field, pair):
+    """-D[to, from minus to] psi (Eq. blkdec) against the oracle's sparse D built from the
+    covariant derivatives: overlapping time slabs, the whole lattice into a wrapped
+    Dirichlet box, and two halves of the lattice split in a periodic direction (hops
+    across the periodic wrap); host arguments give the same bits."""
+    U, gid = field
+    fb, tb = pair
+    d_from = ddp.ddp_set_domain(ctx, gid, *fb)
+    d_to = ddp.ddp_set_domain(ctx, gid, *tb)
+    nf, nt = int(np.prod(fb[1])), int(np.prod(tb[1]))
+    rng = np.random.default_rng(4)
+    psi = rng.standard_normal((3, nf, 4, 3)) + 1j * rng.standard_normal((3, nf, 4, 3))
+    want = dense.boundary_source(U, LAT, AP, fb, psi, tb)
+    sig = torch.zeros((3, nt, 4, 3), dtype=torch.complex128, device="cuda")
+    ddp.ddp_boundary_source(ctx, d_from, torch.from_numpy(psi).cuda(), d_to, sig, 3)
+    got = sig.cpu().numpy()
+    assert max(_col_errors(got, want)) < 1e-12
+    host = np.zeros((3, nt, 4, 3), dtype=np.complex128)
+    ddp.ddp_boundary_source(ctx, d_from, psi, d_to, host, 3)
+    assert np.array_equal(host, got)
+
+
+def test_factorized_propagator(ddp, ctx, field):
+    """S^(f) = -D^-1_{Gamma*_0} D_{dGamma*_0} D^-1_{Gamma-bar_0} (Eq. approxlong) through the
+    C ABI -- mixed-precision solve on Gamma-bar_0, boundary source, solve on Gamma*_0 --
+    against the oracle's same three steps; and its pion contraction (Eq. W0pc with S^(f))."""
+    U, gid = field
+    src = (1, 1, 2, 3)                  # in Gamma-bar_0, outside Gamma*_0
+    kappa = 0.124
+    d_bar = ddp.ddp_set_domain(ctx, gid, *GB0)
+    d_star = ddp.ddp_set_domain(ctx, gid, *GS0)
+    nb, ns = int(np.prod(GB0[1])), int(np.prod(GS0[1]))
+    Sb = torch.zeros((12, nb, 4, 3), dtype=torch.complex128, device="cuda")
+    rc, info = ddp.ddp_solve_propagator(ctx, d_bar, kappa, 0.0, src, 1e-10, ddp.DDP_PREC_MIXED_FP32, Sb)
+    assert rc == ddp.DDP_OK
+    sig = torch.zeros((12, ns, 4, 3), dtype=torch.complex128, device="cuda")
+    ddp.ddp_boundary_source(ctx, d_bar, Sb, d_star, sig, 12)
+    Sf = torch.zeros((12, ns, 4, 3), dtype=torch.complex128, device="cuda")
+    rc, info = ddp.ddp_solve_sources(ctx, d_star, kappa, 0.0, sig, 12, 1e-10, ddp.DDP_PREC_MIXED_FP32, Sf)
+    assert rc == ddp.DDP_OK
+    Sbo, *_ = oracle.propagator(U, LAT, AP, *GB0, kappa, src)
+    sig_o = dense.boundary_source(U, LAT, AP, GB0, Sbo, GS0)
+    Sfo, *_ = oracle.solve(U, LAT, AP, *GS0, kappa, sig_o)
+    assert max(_col_errors(Sf.cpu().numpy(), Sfo)) < COL_TOL
+    C = np.zeros(2 * LAT[0])
+    ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PION, d_star, Sf, C)
+    assert _rel(C[0::2], oracle.pion(LAT, *GS0, Sfo)) < CORR_TOL
 
 
 def test_gauge_region_variant(ddp, ctx, field):
