@@ -372,6 +372,8 @@ def run_other(args):
         res = workloads.batch_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
     elif args.workload == "multilevel":
         res = workloads.multilevel_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
+    elif args.workload == "next":
+        res = workloads.next_rows_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
     else:
         res = workloads.serve_workload(ddp, torch, ctx, synth, prec)
     res["clocks"] = clocks.stop()
@@ -419,7 +421,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", default="slabs", choices=["slabs", "batch", "multilevel", "serve"],
+    ap.add_argument("--workload", default="slabs", choices=["slabs", "batch", "multilevel", "serve", "next"],
                     help="slabs: the benchmark line; the others print their own measurement line")
     ap.add_argument("--param", action="append", default=[],
                     help="solver parameter name=value passed to ddp_set_param (repeatable)")
@@ -428,9 +430,9 @@ def main():
     args = ap.parse_args()
     long_steps = args.workload == "multilevel"
     if args.steps is None:
-        args.steps = 1 if long_steps else 5
+        args.steps = 1 if long_steps else (2 if args.workload == "next" else 5)
     if args.warmup is None:
-        args.warmup = 0 if long_steps else 3
+        args.warmup = 0 if long_steps else (1 if args.workload == "next" else 3)
     if args.warmup < 3 and args.workload == "slabs":
         args.warmup = 3
     if args.impl == "reference":

@@ -137,6 +137,76 @@ def multilevel_workload(ddp, torch, ctx, synth, precision, nvar=32, batch=8, ste
                                                  "(variant generation excluded)", "steps": steps}
 
 
+# -------------------------------------------- factorized propagator, expanded trace
+
+def next_rows_workload(ddp, torch, ctx, synth, precision, steps=2, warmup=1, L=None, x0_cut=24, delta=8):
+    """48 x 24^3 lattice, kappa 0.140.  (1) The factorized propagator of Eq. approxlong
+    with x0_cut = 24 and Delta = 8: Gamma-bar_0 = time slices [0, 32), Gamma*_0 =
+    [24, 48); a 12-column point source at the origin solved on Gamma-bar_0, the boundary
+    source, the 12 columns solved on Gamma*_0, the pion contraction of S^(f).  (2) The
+    expanded stochastic trace of Eq. HPEtr (p = 8) on Gamma-bar_0: psi = D^-1 g5 eta for
+    12 diluted noise columns, (kappa D_hop)^8 psi, contraction with g5 eta."""
+    L = tuple(L or synth.SLAB_LATTICE)
+    kappa = 0.140
+    U = synth.gauge_field_torch(L, seed=synth.SEED_GAUGE, device="cuda")
+    bar = ((0, 0, 0, 0), (x0_cut + delta, L[1], L[2], L[3]))
+    star = ((x0_cut, 0, 0, 0), (L[0] - x0_cut, L[1], L[2], L[3]))
+    nb, ns = int(np.prod(bar[1])), int(np.prod(star[1]))
+    g5 = torch.tensor([-1.0, -1.0, 1.0, 1.0], dtype=torch.float64, device="cuda").view(1, 1, 4, 1)
+    eta = torch.from_numpy(synth.diluted_noise_columns(synth.noise_field(nb, synth.SEED_NOISE0))).cuda()
+    g5eta = (eta * g5).contiguous()
+    Sb = torch.empty((12, nb, 4, 3), dtype=torch.complex128, device="cuda")
+    sig = torch.empty((12, ns, 4, 3), dtype=torch.complex128, device="cuda")
+    Sf = torch.empty((12, ns, 4, 3), dtype=torch.complex128, device="cuda")
+    psi = torch.empty((12, nb, 4, 3), dtype=torch.complex128, device="cuda")
+    v = torch.empty((12, nb, 4, 3), dtype=torch.complex128, device="cuda")
+    Cpi = torch.zeros(2 * L[0], dtype=torch.float64, device="cuda")
+    Ctr = torch.zeros(2 * L[0], dtype=torch.float64, device="cuda")
+    gid = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
+    d_bar = ddp.ddp_set_domain(ctx, gid, *bar)
+    d_star = ddp.ddp_set_domain(ctx, gid, *star)
+    res = {}
+
+    def factorized():
+        rc1, i1 = ddp.ddp_solve_propagator(ctx, d_bar, kappa, 0.0, (0, 0, 0, 0), 1e-10, precision, Sb)
+        ddp.ddp_boundary_source(ctx, d_bar, Sb, d_star, sig, 12)
+        rc2, i2 = ddp.ddp_solve_sources(ctx, d_star, kappa, 0.0, sig, 12, 1e-10, precision, Sf)
+        ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PION, d_star, Sf, Cpi)
+        res["factorized_residuals"] = [i1.max_rel_residual, i2.max_rel_residual]
+        return rc1 or rc2
+
+    def expanded():
+        rc, i = ddp.ddp_solve_sources(ctx, d_bar, kappa, 0.0, g5eta, 12, 1e-10, precision, psi)
+        ddp.ddp_hop_power(ctx, d_bar, kappa, 8, psi, v, 12)
+        ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_NOISE, d_bar, v, Ctr, eta=g5eta, ncol=12)
+        res["expanded_residual"] = i.max_rel_residual
+        return rc
+
+    out = {}
+    for name, fn in (("factorized", factorized), ("expanded", expanded)):
+        for _ in range(warmup):
+            fn()
+        a, b = _events(torch)
+        torch.cuda.synchronize()
+        a.record()
+        rc = 0
+        for _ in range(steps):
+            rc = rc or fn()
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = {"s_per_step": a.elapsed_time(b) / 1e3 / steps, "status": rc}
+    ddp.ddp_free_domain(ctx, d_bar)
+    ddp.ddp_free_domain(ctx, d_star)
+    ddp.ddp_free_gauge(ctx, gid)
+    return {"workload": "48x24^3, kappa 0.140: factorized propagator (Eq. approxlong, x0_cut 24, Delta 8: "
+                        "solve on t in [0,32), boundary source, solve on t in [24,48), pion) and expanded "
+                        "noise trace (Eq. HPEtr, p 8, 12 diluted columns on t in [0,32))",
+            "factorized_s_per_propagator": out["factorized"]["s_per_step"],
+            "expanded_trace_s_per_estimate": out["expanded"]["s_per_step"],
+            "status": [out["factorized"]["status"], out["expanded"]["status"]],
+            "max_rel_residuals": res, "steps": steps, "warmup": warmup}
+
+
 # ----------------------------------------------------------------------- serving
 
 SERVE_CLASSES = [((4, 4, 4, 4), 0.1555), ((8, 8, 8, 8), 0.1555), ((4, 32, 32, 32), 0.1555),
