@@ -204,7 +204,8 @@ int ddp_series_terms(ddp_ctx *ctx, int domain_small, const double *S_small, int 
  * D^{-1}_{Gamma*_0} sigma (ddp_solve_sources) is the factorized propagator
  * S^(f) = -D^{-1}_{Gamma*_0} D_{dGamma*_0} D^{-1}_{Gamma-bar_0} of Eq. approxlong.
  * FP64.  psi [ncol][n_from][4][3], sigma [ncol][n_to][4][3] complex,
- * domain-local lexicographic order, host or device memory.
+ * domain-local lexicographic order, host or device memory; psi and sigma must
+ * not overlap.  Returns when sigma is complete.
  * DDP_ERR_INVALID_ARG for ncol < 1 or domains of different gauge fields. */
 int ddp_boundary_source(ddp_ctx *ctx, int domain_from, const double *psi, int domain_to, double *sigma, int ncol);
 
