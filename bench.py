@@ -225,19 +225,124 @@ def timed(torch, fn, steps, dist=None):
     return start.elapsed_time(end) / 1e3
 
 
-def cpu_oracle_sample(U, kappa):
-    """The FP64 oracle, as it stands, on one column of each of the two thinnest
-    slabs: 2 of the step's 48 column-solves, i.e. 1/6 of a step's 4 solves per
-    12 columns -> (2/12) propagator solves."""
+CPU_SAMPLE = "1 of the 12 columns of the 8-thick and of the 16-thick slab propagators (2 of the step's 48 " \
+             "column-solves, the two cheapest domains of the step)"
+
+
+def oracle_columns(U, kappa, boxes_, tol):
+    """Column 0 (spin 0, colour 0) of the point-source propagator of each box, solved
+    by the FP64 oracle as it stands; returns (seconds, columns)."""
     import oracle
+    cols = []
     t0 = time.perf_counter()
-    for b in boxes()[:2]:
+    for b in boxes_:
         n = b.n_sites
         eta = np.zeros((1, n, 4, 3), dtype=np.complex128)
         eta[0, oracle.local_index(L, b.origin, b.extent, SRC), 0, 0] = 1.0
-        oracle.solve(U, L, oracle.BC_ANTIPERIODIC, b.origin, b.extent, kappa, eta, tol=TOL)
-    dt = time.perf_counter() - t0
-    return (2.0 / 12.0) / dt, dt
+        psi, _, _, _ = oracle.solve(U, L, oracle.BC_ANTIPERIODIC, b.origin, b.extent, kappa, eta, tol=tol)
+        cols.append(psi[0])
+    return time.perf_counter() - t0, cols
+
+
+def cpu_oracle_sample(U, kappa):
+    """The timed CPU baseline: the oracle on column 0 of the 8- and the 16-thick slab
+    propagators at the metric's tolerance, 2 of the step's 48 column-solves."""
+    return oracle_columns(U, kappa, boxes()[:2], TOL)
+
+
+def cpu_baseline_line(dt, cores):
+    """The timed oracle sample as it was run: 2 column-solves in dt seconds; `value`
+    expresses those 2 column-solves in the metric's unit (12 column-solves make one
+    propagator solve), with no other extrapolation."""
+    return {"value": (2.0 / 12.0) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "column_solves_per_s": 2.0 / dt, "timed": "2 of 48 column-solves of one step",
+            "seconds": dt, "sample": CPU_SAMPLE + f", {dt:.1f} s of FP64 CPU work at the metric's tolerance "
+                                                 f"{TOL}; value = (2/12) propagator solves / time"}
+
+
+def _rel(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def parity_block(ddp, torch, ctx, wl, U, cpu_cols):
+    """Error of the measured run against the FP64 oracle.
+    columns: the GPU columns the CPU leg solved, relative L2 error per column and of
+      the pion correlator of that column;
+    propagators: every column of every propagator, the oracle's own true residual
+      |eta - D_Gamma psi_gpu| / |eta| (oracle operator, FP64);
+    correlators: every correlator of the step, relative L2 error of the GPU value
+      against the oracle's contraction of the same propagator."""
+    import oracle
+    out = {"columns": [], "propagators": [], "correlators": []}
+    S_host = [o.cpu().numpy() for o in wl.outs]
+    for i, (b, ref) in enumerate(zip(wl.bx[:2], cpu_cols)):
+        got = S_host[i][0]
+        pi_ref = oracle.pion(L, b.origin, b.extent, ref[None])
+        pi_gpu = oracle.pion(L, b.origin, b.extent, got[None])
+        out["columns"].append({"domain": list(b.extent), "column": 0, "rel_l2_error": _rel(got, ref),
+                               "pion_rel_l2_error": _rel(pi_gpu, pi_ref)})
+    for i, b in enumerate(wl.bx):
+        S = S_host[i]
+        eta = np.zeros_like(S)
+        l = oracle.local_index(L, b.origin, b.extent, SRC)
+        for c in range(12):
+            eta[c, l, c // 3, c % 3] = 1.0
+        r = eta - oracle.apply_dirac(U, L, oracle.BC_ANTIPERIODIC, b.origin, b.extent, KAPPA, S)
+        rr = [float(np.linalg.norm(r[c]) / np.linalg.norm(eta[c])) for c in range(12)]
+        out["propagators"].append({"domain": list(b.extent), "oracle_max_rel_residual": max(rr)})
+        C = wl.C[i].cpu().numpy()
+        nuc = oracle.nucleon(L, b.origin, b.extent, S)
+        pio = oracle.pion(L, b.origin, b.extent, S)
+        ltr = oracle.local_trace(L, b.origin, b.extent, S, SRC)
+        tr = wl.trace[i].cpu().numpy()
+        out["correlators"].append({"domain": list(b.extent),
+                                   "nucleon_rel_l2_error": _rel(C[0, 0::2] + 1j * C[0, 1::2], nuc),
+                                   "pion_rel_l2_error": _rel(C[1, 0::2], pio),
+                                   "local_trace_rel_error": abs(complex(tr[0], tr[1]) - ltr) / abs(ltr)})
+    out["max_column_rel_l2_error"] = max(c["rel_l2_error"] for c in out["columns"])
+    out["max_oracle_rel_residual"] = max(p["oracle_max_rel_residual"] for p in out["propagators"])
+    out["max_correlator_rel_l2_error"] = max(max(c["nucleon_rel_l2_error"], c["pion_rel_l2_error"],
+                                                 c["local_trace_rel_error"]) for c in out["correlators"])
+    out["tolerances"] = {"column": 1e-8, "correlator": 1e-7}
+    return out
+
+
+HOP_KERNELS = (("plain", "DDP_HOP_PLAIN", 2, "tmp = H_oe p"),
+               ("schur_rhat", "DDP_HOP_SCHUR_RHAT", 1, "v = p - k^2 H_eo tmp; (rh, v)"),
+               ("schur_ts", "DDP_HOP_SCHUR_TS", 1, "t = s - k^2 H_eo tmp; (t, s), (t, t)"))
+
+
+def stencil_roofline(ddp, ctx, U_dev, prec, precision_name, iters=50):
+    """CUDA-event time of every inner-loop stencil variant on the full 48x24^3 domain
+    with 12 columns; the dominant one (largest share of a BiCGStab iteration:
+    launches per iteration x time per launch) is the roofline kernel."""
+    gid = ddp.ddp_load_gauge(ctx, U_dev, L, ddp.DDP_BC_ANTIPERIODIC)
+    did = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), L)
+    peak, peak_kind = measured_peaks()
+    rec = hop_traffic_record()
+    per = {}
+    for name, const, per_iter, what in HOP_KERNELS:
+        ms, nbytes = ddp.ddp_time_hop(ctx, did, KAPPA, 12, prec, iters, getattr(ddp, const))
+        achieved = nbytes / (ms * 1e-3) / 1e9
+        traffic = None
+        if rec:
+            traffic = rec.get("kernels", {}).get(f"{precision_name}/{name}")
+        per[name] = {"computes": what, "launches_per_iteration": per_iter, "ms_per_launch": ms,
+                     "algorithmic_bytes_per_launch": nbytes, "achieved": achieved, "frac": achieved / peak,
+                     "traffic": traffic}
+    ddp.ddp_free_domain(ctx, did)
+    ddp.ddp_free_gauge(ctx, gid)
+    tot = sum(v["launches_per_iteration"] * v["ms_per_launch"] for v in per.values())
+    for v in per.values():
+        v["share_of_stencil_time"] = v["launches_per_iteration"] * v["ms_per_launch"] / tot
+    dom = max(per, key=lambda k: per[k]["share_of_stencil_time"])
+    d = per[dom]
+    return {"bound": "hbm", "achieved": d["achieved"], "peak": peak, "unit": "GB/s", "frac": d["frac"],
+            "traffic": d["traffic"], "kernel": f"k_hop<{precision_name}> {dom}: {d['computes']}",
+            "ms_per_launch": d["ms_per_launch"], "algorithmic_bytes_per_launch": d["algorithmic_bytes_per_launch"],
+            "launch": "48x24^3 full lattice, 12 columns, 3,981,312 output site-columns",
+            "peak_kind": f"{peak_kind} HBM copy bandwidth", "per_kernel": per}
 
 
 def run_gpu(args):
@@ -302,18 +407,9 @@ def run_gpu(args):
                 "max_rel_residual": max(i.max_rel_residual for i in wl64.infos)}
         del wl64
 
-    # roofline of the dominant kernel: the inner-loop Schur-complement stencil
-    gid = ddp.ddp_load_gauge(ctx, wl.U_dev, L, ddp.DDP_BC_ANTIPERIODIC)
-    did = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), L)
-    ms, algo_bytes = ddp.ddp_time_hop(ctx, did, KAPPA, 12, prec, 50)
-    ddp.ddp_free_domain(ctx, did)
-    ddp.ddp_free_gauge(ctx, gid)
-    peak, peak_kind = measured_peaks()
-    achieved = algo_bytes / (ms * 1e-3) / 1e9
-    rec = hop_traffic_record()
-    traffic = None
-    if rec and rec.get("precision") == args.precision:
-        traffic = rec.get("dram_bytes_per_launch_full")
+    roof = stencil_roofline(ddp, ctx, wl.U_dev, prec, args.precision)
+    col_iters = sum(i["column_iters"] for i in infos)
+    site_col_iters = sum(i["column_iters"] * b.n_sites // 2 for i, b in zip(infos, wl.bx))
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -332,20 +428,23 @@ def run_gpu(args):
                 "pinned_GBps": link},
         "gpu_launches": int(launches),
         "clocks": clk,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": f"k_hop<{args.precision}, MHAT, RHAT>",
-                     "ms_per_launch": ms, "algorithmic_bytes_per_launch": algo_bytes,
-                     "peak_kind": f"{peak_kind} HBM copy bandwidth"},
+        "roofline": roof,
+        # kappa-independent throughput of the inner solver: BiCGStab iterations of single
+        # columns (and of even site-columns) per second, summed over the step's 48 columns
+        "column_iterations_per_s": col_iters * args.steps * world / secs,
+        "site_column_iterations_per_s": site_col_iters * args.steps * world / secs,
+        "inner_iterations_per_step": col_iters,
         "fp64_path": fp64,
         "speedup_vs_fp64": (value / fp64["solves_per_s"]) if fp64 else None,
         "solves": infos,
     }
     if rank == 0 and world == 1 and not args.skip_cpu:
-        v, dt = cpu_oracle_sample(U, KAPPA)
         import oracle
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                                "sample": f"1 of 12 columns of the 8- and 16-thick slab propagators "
-                                          f"({dt:.1f} s of FP64 CPU work), rate per 12-column solve"}
+        dt, _ = cpu_oracle_sample(U, KAPPA)
+        line["cpu_baseline"] = cpu_baseline_line(dt, oracle.num_threads())
+        # parity columns at the oracle's own tolerance (1e-12), so that its error is negligible
+        _, cols = oracle_columns(U, KAPPA, boxes()[:2], 1e-12)
+        line["parity"] = parity_block(ddp, torch, ctx, wl, U, cols)
     ddp.ddp_destroy(ctx)
     if rank == 0:
         print(json.dumps(line))
@@ -385,29 +484,63 @@ def run_other(args):
 
 # ---------------------------------------------------------- reference arm
 
+REF_SAMPLE = "column 0 of the 8-thick slab propagator (1 of the step's 48 column-solves, the step's cheapest domain)"
+
+
 def run_reference(args):
+    """The oracle as it stands on the host cores: per step, one column-solve of the
+    workload (bounded so that the whole run takes a few minutes); value = that
+    column-solve in the metric's unit (1/12 of a propagator solve) per second."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     U = synth.gauge_field(L, seed=synth.SEED_GAUGE)
     for _ in range(args.warmup):
-        cpu_oracle_sample(U, KAPPA)
-    t0 = time.perf_counter()
+        oracle_columns(U, KAPPA, boxes()[:1], TOL)
+    dt = 0.0
     for _ in range(args.steps):
-        cpu_oracle_sample(U, KAPPA)
-    dt = time.perf_counter() - t0
-    value = args.steps * (2.0 / 12.0) / dt
+        d, _ = oracle_columns(U, KAPPA, boxes()[:1], TOL)
+        dt += d
+    value = args.steps * (1.0 / 12.0) / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded SU(3) field, plaquette 0.59)",
             "config": {"workload": f"48x24^3 nested time slabs 8/16/24 + full lattice, 12-column point-source "
                                    f"propagators, kappa {KAPPA}, tol {TOL}", "kappa": KAPPA},
-            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": value,
-                             "sample": "per step: 1 of 12 columns of the 8- and 16-thick slab propagators"},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": value, "unit": UNIT,
+                             "column_solves_per_s": args.steps / dt, "timed": "1 of 48 column-solves per step",
+                             "sample": "per step: " + REF_SAMPLE + f", at tolerance {TOL}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def run_hop(args):
+    """One stencil variant alone on a whole lattice (the ncu target for the stencil
+    profiles): average CUDA-event time of `--iters` launches and the bandwidth its
+    algorithmic bytes imply."""
+    import torch
+
+    import paper_1601_04587_gb300 as ddp
+
+    Lh = tuple(args.lattice)
+    U = synth.gauge_field_torch(Lh, seed=synth.SEED_GAUGE, device="cuda")
+    ctx = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    for kv in args.param:
+        k, v = kv.split("=")
+        ddp.ddp_set_param(ctx, k, float(v))
+    gid = ddp.ddp_load_gauge(ctx, U, Lh, ddp.DDP_BC_ANTIPERIODIC)
+    did = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), Lh)
+    kern = {"plain": ddp.DDP_HOP_PLAIN, "schur_rhat": ddp.DDP_HOP_SCHUR_RHAT, "schur_ts": ddp.DDP_HOP_SCHUR_TS}
+    res = {}
+    for name in (args.kernel.split(",") if args.kernel != "all" else list(kern)):
+        ms, nbytes = ddp.ddp_time_hop(ctx, did, KAPPA, args.ncol, ddp.PRECISIONS[args.precision], args.iters,
+                                      kern[name])
+        res[name] = {"ms_per_launch": ms, "algorithmic_bytes": nbytes, "GBps": nbytes / ms / 1e6}
+    ddp.ddp_destroy(ctx)
+    print(json.dumps({"workload": "hop", "lattice": Lh, "ncol": args.ncol, "precision": args.precision,
+                      "kernels": res}))
 
 
 def main():
@@ -421,8 +554,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", default="slabs", choices=["slabs", "batch", "multilevel", "serve", "next"],
+    ap.add_argument("--workload", default="slabs", choices=["slabs", "batch", "multilevel", "serve", "next", "hop"],
                     help="slabs: the benchmark line; the others print their own measurement line")
+    ap.add_argument("--lattice", type=int, nargs=4, default=[32, 24, 24, 24], help="--workload hop: lattice")
+    ap.add_argument("--kernel", default="all", help="--workload hop: plain, schur_rhat, schur_ts or all")
+    ap.add_argument("--ncol", type=int, default=12, help="--workload hop: columns")
+    ap.add_argument("--iters", type=int, default=20, help="--workload hop: timed launches per kernel")
     ap.add_argument("--param", action="append", default=[],
                     help="solver parameter name=value passed to ddp_set_param (repeatable)")
     ap.add_argument("--no-conditional", action="store_true",
@@ -433,10 +570,12 @@ def main():
         args.steps = 1 if long_steps else (2 if args.workload == "next" else 5)
     if args.warmup is None:
         args.warmup = 0 if long_steps else (1 if args.workload == "next" else 3)
-    if args.warmup < 3 and args.workload == "slabs":
+    if args.warmup < 3 and args.workload == "slabs" and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "hop":
+        run_hop(args)
     elif args.workload != "slabs":
         run_other(args)
     else:

@@ -93,6 +93,7 @@ typedef struct {
     double max_rel_residual;                    /* max over columns of |eta - D_Gamma psi| / |eta| (FP64) */
     double rel_residual[DDP_INFO_COLS];         /* per column, first DDP_INFO_COLS columns */
     double seconds;         /* wall time of the call */
+    int64_t column_iters;   /* BiCGStab iterations summed over columns and outer cycles */
 } ddp_solve_info;
 
 typedef struct ddp_ctx ddp_ctx;
@@ -271,19 +272,30 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * chunks).  DDP_ERR_INVALID_ARG for unknown names or values. */
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value);
 
-/* Average duration (ms) of the inner-loop stencil kernel (Schur-complement
- * hop with fused epilogue and dot product) on a domain with ncol columns in
- * the given storage format, timed with CUDA events over `iters` launches on
- * the context's stream; bytes_per_launch receives the kernel's algorithmic
- * HBM bytes (input, operand, shadow residual and output spinors plus
- * the links touching the output sites). */
-int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters,
+/* Inner-loop stencil variants, for ddp_time_hop: one BiCGStab iteration on the
+ * even-odd Schur complement runs PLAIN twice and each SCHUR variant once. */
+typedef enum {
+    DDP_HOP_PLAIN = 0,        /* tmp = H_oe p (odd output sites) */
+    DDP_HOP_SCHUR_RHAT = 1,   /* v = p - kappa^2 H_eo tmp, with the (rh, v) partial sums */
+    DDP_HOP_SCHUR_TS = 2      /* t = s - kappa^2 H_eo tmp, with the (t, s), (t, t) partial sums */
+} ddp_hop_kernel;
+
+/* Average duration (ms) of one inner-loop stencil variant (ddp_hop_kernel) on
+ * a domain with ncol columns in the given storage format, timed with CUDA
+ * events over `iters` launches on the context's stream after 3 warm-up
+ * launches; bytes_per_launch receives the variant's algorithmic HBM bytes:
+ * the spinors it reads or writes once per output site-column (2 for PLAIN,
+ * 4 for SCHUR_RHAT, 3 for SCHUR_TS) plus the 8 links touching every output
+ * site once for all columns. */
+int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int kernel, int iters,
                  float *ms_per_launch, double *bytes_per_launch);
 
-/* Autotuner: times the inner-loop stencil on the domain (ncol columns, the
- * given storage format, iters launches each) for every admissible number of
- * columns per thread block, keeps the fastest for that storage format in the
- * context (used by every later solve with that format) and returns it. */
+/* Autotuner: times the three inner-loop stencil variants on the domain (ncol
+ * columns, the given storage format, iters launches each) for every admissible
+ * number of columns per thread block, keeps the choice with the shortest
+ * stencil time per BiCGStab iteration (2 x PLAIN + SCHUR_RHAT + SCHUR_TS) for
+ * that storage format in the context (used by every later solve with that
+ * format) and returns it with that time. */
 int ddp_autotune(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters, int *best_cols,
                  float *best_ms);
 
@@ -304,15 +316,25 @@ int ddp_serve_reset(ddp_ctx *ctx);
  * of DDP_STATIC_PARTIALS_MAX double2 entries (2 MiB) that lives in the
  * library and stays held on every GPU that loads it until the process exits.
  *
- *  - S, eta (noise kind only) and C_out must be device pointers; C_out gets
- *    2*L[0] doubles (2 for PSEUDO_LOCAL).  Geometry as in ddp_set_domain.
+ *  - S, eta (noise kind only) and C_out must be device (or managed) memory of
+ *    the current device; host memory, pinned or not, and memory of another
+ *    device are refused with DDP_ERR_INVALID_ARG before anything is enqueued.
+ *    The caller also guarantees their sizes: S (and eta) hold ncol * n_sites *
+ *    12 complex doubles (ncol = 12 except for PION and PSEUDO_NOISE), C_out
+ *    2*L[0] doubles (2 for PSEUDO_LOCAL).  Geometry as in ddp_set_domain: an
+ *    extent outside [1, L] is DDP_ERR_INVALID_ARG, an odd L[mu] or an odd
+ *    extent[3] DDP_ERR_UNSUPPORTED.
+ *  - A CUDA error already pending in the calling thread when the call starts
+ *    is returned as DDP_ERR_CUDA and left pending (nothing is launched).
  *  - The partial sums need extent[0] * ceil(extent[1]*extent[2]*extent[3] / T)
  *    entries with T = 32 for NUCLEON and 128 otherwise; more than
  *    DDP_STATIC_PARTIALS_MAX returns DDP_ERR_INVALID_ARG and launches nothing.
  *  - The first call on a device looks up the device address of the array
  *    (cudaGetSymbolAddress, with that device current); make that first call
  *    before any stream capture.  Later calls only enqueue kernels on
- *    cuda_stream.
+ *    cuda_stream.  The address is kept for the life of the process and is
+ *    valid for the device's primary context only: after cudaDeviceReset, or
+ *    with another context current, do not call this entry point again.
  *  - All calls share the array.  Each call writes every entry it reads, so
  *    nothing has to be cleared between calls, but calls that may overlap on
  *    the GPU (different streams without ordering between them) race on it.

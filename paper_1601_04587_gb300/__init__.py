@@ -22,6 +22,7 @@ DDP_ERR_NOT_CONVERGED, DDP_ERR_CUDA, DDP_ERR_BUSY, DDP_ERR_NOT_FOUND = 4, 5, 6, 
 DDP_BC_PERIODIC, DDP_BC_ANTIPERIODIC, DDP_BC_OPEN = 0, 1, 2
 DDP_PREC_FP64, DDP_PREC_MIXED_FP32, DDP_PREC_MIXED_FP16, DDP_PREC_MIXED_BF16 = 0, 1, 2, 3
 DDP_CONTRACT_PSEUDO_LOCAL, DDP_CONTRACT_PSEUDO_NOISE, DDP_CONTRACT_NUCLEON, DDP_CONTRACT_PION = 0, 1, 2, 3
+DDP_HOP_PLAIN, DDP_HOP_SCHUR_RHAT, DDP_HOP_SCHUR_TS = 0, 1, 2
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 DDP_INFO_COLS = 12
 
@@ -29,7 +30,8 @@ DDP_INFO_COLS = 12
 class ddp_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("ncol", ctypes.c_int), ("outer_cycles", ctypes.c_int),
                 ("inner_iters", ctypes.c_int), ("max_rel_residual", ctypes.c_double),
-                ("rel_residual", ctypes.c_double * DDP_INFO_COLS), ("seconds", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double * DDP_INFO_COLS), ("seconds", ctypes.c_double),
+                ("column_iters", ctypes.c_int64)]
 
 
 class ddp_solve_req(ctypes.Structure):
@@ -87,7 +89,7 @@ def lib():
             "ddp_poll": ([vp, ctypes.c_uint64, i4, ctypes.POINTER(ddp_solve_info)], i),
             "ddp_serve_reset": ([vp], i),
             "ddp_set_param": ([vp, ctypes.c_char_p, d], i),
-            "ddp_time_hop": ([vp, i, d, i, i, i, ctypes.POINTER(ctypes.c_float),
+            "ddp_time_hop": ([vp, i, d, i, i, i, i, ctypes.POINTER(ctypes.c_float),
                               ctypes.POINTER(ctypes.c_double)], i),
             "ddp_kernel_launches": ([vp], ctypes.c_long),
             "ddp_contract_static": ([i, i4, i4, i4, vp, vp, i, i4, vp, vp], i),
@@ -292,11 +294,12 @@ def ddp_set_param(ctx, name: str, value: float):
     return _check(ctx, lib().ddp_set_param(ctx, name.encode(), float(value)), "ddp_set_param")
 
 
-def ddp_time_hop(ctx, domain_id, kappa, ncol, precision, iters):
+def ddp_time_hop(ctx, domain_id, kappa, ncol, precision, iters, kernel=DDP_HOP_PLAIN):
+    """(ms per launch, algorithmic bytes per launch) of one inner-loop stencil variant."""
     ms = ctypes.c_float()
     by = ctypes.c_double()
-    _check(ctx, lib().ddp_time_hop(ctx, int(domain_id), float(kappa), int(ncol), int(precision), int(iters),
-                                   ctypes.byref(ms), ctypes.byref(by)), "ddp_time_hop")
+    _check(ctx, lib().ddp_time_hop(ctx, int(domain_id), float(kappa), int(ncol), int(precision), int(kernel),
+                                   int(iters), ctypes.byref(ms), ctypes.byref(by)), "ddp_time_hop")
     return ms.value, by.value
 
 
@@ -337,9 +340,29 @@ def ddp_kernel_launches(ctx) -> int:
     return int(lib().ddp_kernel_launches(ctx))
 
 
+def _device_doubles(a, need, what):
+    """Size in doubles of a CUDA complex128/float64 tensor, checked against `need`."""
+    import torch
+    if not isinstance(a, torch.Tensor) or not a.is_cuda:
+        raise DDPError(DDP_ERR_INVALID_ARG, "ddp_contract_static", f"{what} must be a CUDA tensor")
+    if a.dtype not in (torch.complex128, torch.float64):
+        raise DDPError(DDP_ERR_INVALID_ARG, "ddp_contract_static", f"{what} must be complex128 or float64")
+    nd = a.numel() * (2 if a.dtype == torch.complex128 else 1)
+    if nd < need:
+        raise DDPError(DDP_ERR_INVALID_ARG, "ddp_contract_static", f"{what} holds {nd} doubles, needs {need}")
+
+
 def ddp_contract_static(kind, L, origin, extent, S, C_out, eta=None, ncol=12, src=(0, 0, 0, 0), stream=None):
     """Allocation-free contraction for callers that must not allocate device
-    memory (see include/ddp.h); device buffers only, enqueued on `stream`."""
+    memory (see include/ddp.h); CUDA tensors only, enqueued on `stream`.  The
+    tensors' device, dtype and size are checked here; the C entry point checks
+    the pointer kinds again."""
+    n = int(np.prod([int(e) for e in extent]))
+    nc = int(ncol) if kind in (DDP_CONTRACT_PION, DDP_CONTRACT_PSEUDO_NOISE) else 12
+    _device_doubles(S, 2 * 12 * nc * n, "S")
+    if kind == DDP_CONTRACT_PSEUDO_NOISE:
+        _device_doubles(eta, 2 * 12 * nc * n, "eta")
+    _device_doubles(C_out, 2 if kind == DDP_CONTRACT_PSEUDO_LOCAL else 2 * int(L[0]), "C_out")
     s = ctypes.c_void_p(int(stream)) if stream else None
     return _check(None, lib().ddp_contract_static(int(kind), _i4(L), _i4(origin), _i4(extent), _ptr(S), _ptr(eta),
                                                   int(ncol), _i4(src), _ptr(C_out), s), "ddp_contract_static")
@@ -348,5 +371,6 @@ def ddp_contract_static(kind, L, origin, extent, S, C_out, eta=None, ncol=12, sr
 def info_dict(info: ddp_solve_info) -> dict:
     n = min(info.ncol, DDP_INFO_COLS)
     return {"status": info.status, "ncol": info.ncol, "outer_cycles": info.outer_cycles,
-            "inner_iters": info.inner_iters, "max_rel_residual": info.max_rel_residual,
+            "inner_iters": info.inner_iters, "column_iters": int(info.column_iters),
+            "max_rel_residual": info.max_rel_residual,
             "rel_residual": [info.rel_residual[i] for i in range(n)], "seconds": info.seconds}

@@ -111,7 +111,7 @@ int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *ou
 template <class P>
 int hop_power_impl(ddp_ctx *ctx, const Job &job, int p, const double *psi, double *out);
 template <class P>
-int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, double *bytes);
+int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int kernel, int iters, float *ms, double *bytes);
 
 }  // namespace ddp
 
@@ -793,12 +793,12 @@ int ddp_hop_power(ddp_ctx *ctx, int domain_id, double kappa, int p, const double
     return DDP_OK;
 }
 
-// Average duration of the inner-loop stencil kernel (the Schur-complement
-// hop with its fused epilogue and dot product) on a domain, timed with CUDA
-// events on the context's stream over `iters` back-to-back launches.
-int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters, float *ms_per_launch,
-                 double *bytes_per_launch) {
+// Average duration of one inner-loop stencil variant on a domain, timed with
+// CUDA events on the context's stream over `iters` back-to-back launches.
+int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int kernel, int iters,
+                 float *ms_per_launch, double *bytes_per_launch) {
     if (!ctx || ncol < 1 || iters < 1 || !ms_per_launch) return DDP_ERR_INVALID_ARG;
+    if (kernel < DDP_HOP_PLAIN || kernel > DDP_HOP_SCHUR_TS) return DDP_ERR_INVALID_ARG;
     const DomainDev *d;
     const GaugeDev *g;
     int rc = find_domain(ctx, domain_id, &d, &g);
@@ -814,10 +814,10 @@ int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precis
     j.ncol = ncol;
     double bytes = 0;
     switch (precision) {
-        case DDP_PREC_FP64: rc = time_hop_impl<PF64>(ctx, j, precision, iters, ms_per_launch, &bytes); break;
-        case DDP_PREC_MIXED_FP32: rc = time_hop_impl<PF32>(ctx, j, precision, iters, ms_per_launch, &bytes); break;
-        case DDP_PREC_MIXED_FP16: rc = time_hop_impl<PF16>(ctx, j, precision, iters, ms_per_launch, &bytes); break;
-        case DDP_PREC_MIXED_BF16: rc = time_hop_impl<PBF16>(ctx, j, precision, iters, ms_per_launch, &bytes); break;
+        case DDP_PREC_FP64: rc = time_hop_impl<PF64>(ctx, j, precision, kernel, iters, ms_per_launch, &bytes); break;
+        case DDP_PREC_MIXED_FP32: rc = time_hop_impl<PF32>(ctx, j, precision, kernel, iters, ms_per_launch, &bytes); break;
+        case DDP_PREC_MIXED_FP16: rc = time_hop_impl<PF16>(ctx, j, precision, kernel, iters, ms_per_launch, &bytes); break;
+        case DDP_PREC_MIXED_BF16: rc = time_hop_impl<PBF16>(ctx, j, precision, kernel, iters, ms_per_launch, &bytes); break;
         default: return DDP_ERR_INVALID_ARG;
     }
     if (bytes_per_launch) *bytes_per_launch = bytes;
@@ -874,6 +874,7 @@ static int run_solves(ddp_ctx *ctx, const ddp_solve_req *reqs, int n, int precis
             inf.ncol = jobs[i].ncol;
             inf.outer_cycles = ji[i].outer;
             inf.inner_iters = ji[i].inner;
+            inf.column_iters = ji[i].column_iters;
             inf.seconds = secs;
             double mx = 0;
             for (int c = 0; c < jobs[i].ncol; c++) {
@@ -1025,28 +1026,35 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
 
 long ddp_kernel_launches(const ddp_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
-// Autotuner: time the inner-loop stencil on the domain for every admissible
-// number of columns per block and keep the fastest for this storage format.
+// Autotuner: time the three inner-loop stencil variants on the domain for every
+// admissible number of columns per block and keep, for this storage format, the
+// choice with the shortest stencil time of one BiCGStab iteration (two PLAIN
+// launches and one of each Schur variant).
 int ddp_autotune(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters, int *best_cols,
                  float *best_ms) {
     if (!ctx || ncol < 1 || precision < 0 || precision > 3 || iters < 1) return DDP_ERR_INVALID_ARG;
     const int cands[] = {12, 8, 6, 4, 3, 2, 1};
+    const int weight[3] = {2, 1, 1};
     int saved = ctx->prm.CG, best = 0;
     float bms = 0;
     ctx->prm.CG = 0;
     for (int c : cands) {
         if (c > ncol) continue;
         ctx->prm.CG = c;
-        float ms = 0;
-        double by = 0;
-        int rc = ddp_time_hop(ctx, domain_id, kappa, ncol, precision, iters, &ms, &by);
-        if (rc) {
-            ctx->prm.CG = saved;
-            return rc;
+        float tot = 0;
+        for (int k = DDP_HOP_PLAIN; k <= DDP_HOP_SCHUR_TS; k++) {
+            float ms = 0;
+            double by = 0;
+            int rc = ddp_time_hop(ctx, domain_id, kappa, ncol, precision, k, iters, &ms, &by);
+            if (rc) {
+                ctx->prm.CG = saved;
+                return rc;
+            }
+            tot += weight[k] * ms;
         }
-        if (!best || ms < bms) {
+        if (!best || tot < bms) {
             best = c;
-            bms = ms;
+            bms = tot;
         }
     }
     ctx->prm.CG = saved;

@@ -409,6 +409,18 @@ namespace {
 std::mutex g_static_mu;
 double2 *g_static_ptr[64] = {nullptr};  // per device: device address of g_contract_partials
 
+// Device (or managed) memory that the current device can address in kernels.
+bool on_current_device(const void *p, int dev) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" int ddp_contract_static(int kind, const int L[4], const int origin[4], const int extent[4],
@@ -418,10 +430,13 @@ extern "C" int ddp_contract_static(int kind, const int L[4], const int origin[4]
     if (kind < 0 || kind > 3) return DDP_ERR_INVALID_ARG;
     int64_t n = 1;
     for (int m = 0; m < 4; m++) {
-        if (L[m] < 2 || L[m] % 2 || extent[m] < 1 || extent[m] > L[m]) return DDP_ERR_INVALID_ARG;
+        if (L[m] < 2 || extent[m] < 1 || extent[m] > L[m]) return DDP_ERR_INVALID_ARG;
         n *= extent[m];
     }
-    if (extent[3] % 2) return DDP_ERR_INVALID_ARG;
+    // the same geometry ddp_load_gauge and ddp_set_domain accept
+    for (int m = 0; m < 4; m++)
+        if (L[m] % 2) return DDP_ERR_UNSUPPORTED;
+    if (extent[3] % 2) return DDP_ERR_UNSUPPORTED;
     if (kind == DDP_CONTRACT_PSEUDO_NOISE) {
         if (!eta || ncol < 1) return DDP_ERR_INVALID_ARG;
     } else if (kind == DDP_CONTRACT_PION) {
@@ -429,8 +444,14 @@ extern "C" int ddp_contract_static(int kind, const int L[4], const int origin[4]
     } else {
         ncol = 12;
     }
+    // an error left by earlier, unrelated work is the caller's: report it without touching it
+    if (cudaPeekAtLastError() != cudaSuccess) return DDP_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DDP_ERR_CUDA;
+    // kernels are launched on these buffers directly: host memory, or memory of another
+    // device, is refused before anything is enqueued
+    if (!on_current_device(S, dev) || !on_current_device(C_out, dev)) return DDP_ERR_INVALID_ARG;
+    if (kind == DDP_CONTRACT_PSEUDO_NOISE && !on_current_device(eta, dev)) return DDP_ERR_INVALID_ARG;
     double2 *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_static_mu);
@@ -468,7 +489,7 @@ extern "C" int ddp_contract_static(int kind, const int L[4], const int origin[4]
         }
         int l = ((k[0] * extent[1] + k[1]) * extent[2] + k[2]) * extent[3] + k[3];
         k_local_trace<<<1, 1, 0, st>>>((const double2 *)S, n, l, (double2 *)C_out);
-        return cudaGetLastError() == cudaSuccess ? DDP_OK : DDP_ERR_CUDA;
+        return cudaPeekAtLastError() == cudaSuccess ? DDP_OK : DDP_ERR_CUDA;
     }
     int slice_n = extent[1] * extent[2] * extent[3];
     int threads = (kind == DDP_CONTRACT_NUCLEON) ? 32 : 128;
@@ -487,8 +508,9 @@ extern "C" int ddp_contract_static(int kind, const int L[4], const int origin[4]
         k_contract_nucleon<<<grid, NUC_WARPS * 32, 0, st>>>(a);
     else
         k_contract_slice<<<grid, threads, 0, st>>>(a);
+    if (cudaPeekAtLastError() != cudaSuccess) return DDP_ERR_CUDA;
     k_contract_final<<<L[0], 256, 0, st>>>(it, scratch, nchunk, (double2 *)C_out);
-    return cudaGetLastError() == cudaSuccess ? DDP_OK : DDP_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? DDP_OK : DDP_ERR_CUDA;
 }
 
 // ------------------------------------------- two-level factorized correlator

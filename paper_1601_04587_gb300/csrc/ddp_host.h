@@ -57,6 +57,7 @@ struct JobInfo {
     int status = DDP_OK;
     int outer = 0;
     int inner = 0;
+    int64_t column_iters = 0;  // inner iterations summed over columns
     std::vector<double> relres;
 };
 

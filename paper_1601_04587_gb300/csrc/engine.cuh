@@ -395,6 +395,7 @@ struct Engine {
                 inf.relres[c] = rr;
                 ok = ok && (rr <= jobs[i].tol);
                 inner = std::max(inner, S.total_iters);
+                inf.column_iters += S.total_iters;
             }
             inf.inner = inner;
             inf.status = ok ? DDP_OK : DDP_ERR_NOT_CONVERGED;
@@ -536,13 +537,17 @@ int hop_power_impl(ddp_ctx *ctx, const Job &job, int p, const double *psi, doubl
     return DDP_OK;
 }
 
-// Timing of the inner-loop stencil kernel v = p - kappa^2 H_eo tmp with the
-// fused (rh, v) partials, on fields of the given domain (contents: a packed
-// unit source, which does not change the kernel's work).  Algorithmic bytes
-// per launch: input half-field, epilogue operand, shadow residual and output
-// (4 x 24 reals per site-column) plus every link of the domain once.
+// Timing of one inner-loop stencil variant on fields of the given domain
+// (contents: zeros, which does not change the kernel's work), CUDA events on
+// the context's stream around `iters` back-to-back launches after 3 warm-up
+// launches.  kernel: DDP_HOP_PLAIN  tmp = H_oe p;  DDP_HOP_SCHUR_RHAT  v = p -
+// kappa^2 H_eo tmp with the (rh, v) partials;  DDP_HOP_SCHUR_TS  t = s -
+// kappa^2 H_eo tmp with the (t, s), (t, t) partials.  Algorithmic bytes per
+// launch: the spinors the variant reads or writes once per output
+// site-column (2, 4 and 3 of them) plus the 8 links touching each output
+// site once for all columns.
 template <class P>
-int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, double *bytes) {
+int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int kernel, int iters, float *ms, double *bytes) {
     std::vector<Job> jobs(1, job);
     Plan plan;
     make_plan(jobs, prec, ctx->prm, plan);
@@ -578,32 +583,42 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int iters, float *ms, 
     h.st = nullptr;
     h.skip = 0;
     h.L = L;
-    h.p = 0;
+    h.p = (kernel == DDP_HOP_PLAIN) ? 1 : 0;
     h.in = in;
     h.out = out;
-    h.v1 = v1;
+    h.v1 = (kernel == DDP_HOP_PLAIN) ? none : v1;
     h.v2 = none;
-    h.rh = rhv;
+    h.rh = (kernel == DDP_HOP_SCHUR_RHAT) ? rhv : none;
     h.part = A;
+    auto launch = [&]() {
+        if (kernel == DDP_HOP_PLAIN)
+            launch_hop<P, EPI_PLAIN, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+        else if (kernel == DDP_HOP_SCHUR_RHAT)
+            launch_hop<P, EPI_MHAT, DOT_RHAT>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+        else
+            launch_hop<P, EPI_MHAT, DOT_TS>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+    };
     cudaEvent_t e0, e1;
     DDP_CUDA(ctx, cudaEventCreate(&e0));
     DDP_CUDA(ctx, cudaEventCreate(&e1));
-    for (int i = 0; i < 3; i++) launch_hop<P, EPI_MHAT, DOT_RHAT>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+    for (int i = 0; i < 3; i++) launch();
     DDP_CUDA(ctx, cudaEventRecord(e0, st));
-    for (int i = 0; i < iters; i++) launch_hop<P, EPI_MHAT, DOT_RHAT>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+    for (int i = 0; i < iters; i++) launch();
     DDP_CUDA(ctx, cudaEventRecord(e1, st));
     DDP_CUDA(ctx, cudaEventSynchronize(e1));
     float t = 0;
     DDP_CUDA(ctx, cudaEventElapsedTime(&t, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    DDP_CUDA(ctx, cudaGetLastError());
     ctx->launches += 3 + iters;
     *ms = t / iters;
-    double site_cols = (double)plan.items[0].nh * job.ncol;
-    double spinor = (double)sizeof(typename P::chunk) * P::NCH + (P::SCALED ? 4.0 : 0.0);
-    double link = P::IS64 ? 144.0 : (double)sizeof(typename P::chunk) * 0 + (std::is_same<P, PF32>::value ? 48.0 : 24.0);
-    // every link touching the output parity: 8 per output site (4 forward + 4 backward)
-    *bytes = site_cols * 4.0 * spinor + (double)plan.items[0].nh * 8.0 * link;
+    const double site_cols = (double)plan.items[0].nh * job.ncol;
+    const double spinor = (double)sizeof(typename P::chunk) * P::NCH + (P::SCALED ? 4.0 : 0.0);
+    const double link = P::IS64 ? 144.0 : (std::is_same<P, PF32>::value ? 48.0 : 24.0);
+    const int nspinor = (kernel == DDP_HOP_PLAIN) ? 2 : (kernel == DDP_HOP_SCHUR_RHAT) ? 4 : 3;
+    // every link touching an output site: 8 per output site (4 forward + 4 backward)
+    *bytes = site_cols * nspinor * spinor + (double)plan.items[0].nh * 8.0 * link;
     return DDP_OK;
 }
 

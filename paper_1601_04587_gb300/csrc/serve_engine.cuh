@@ -188,6 +188,7 @@ struct Server : ServerBase {
             inf.outer_cycles = r.outer;
             double mx = 0;
             int inner = 0;
+            int64_t colit = 0;
             bool ok = true;
             for (int c = 0; c < it.ncol; c++) {
                 const SolveState &S = r.st[c];
@@ -196,9 +197,11 @@ struct Server : ServerBase {
                 if (!(rr <= mx)) mx = rr;
                 ok = ok && (rr <= r.job.tol);
                 inner = std::max(inner, S.total_iters);
+                colit += S.total_iters;
             }
             inf.max_rel_residual = mx;
             inf.inner_iters = inner;
+            inf.column_iters = colit;
             inf.status = ok ? DDP_OK : DDP_ERR_NOT_CONVERGED;
             release(r.off, r.len);
         }

@@ -70,15 +70,62 @@ def test_static_matches_allocating_entry_point_twice(ddp, setup, kind):
             ddp.ddp_contract_static(k, L, o, e, S, got, eta=eta, ncol=12, src=src, stream=stream)
             torch.cuda.synchronize()
             g = got.cpu().numpy()
-            assert np.all(np.isfinite(g))
-            assert _rel(g, want) <= CORR_TOL
+            # same kernels and the same reduction order as ddp_contract: identical bits
+            assert np.array_equal(g, want)
         ddp.ddp_free_domain(ctx, did)
 
 
+def test_static_nucleon_matches_oracle(ddp, setup):
+    """One case against the FP64 oracle directly, on an oracle propagator."""
+    import oracle
+    ctx, gid, L = setup
+    o, e = (0, 0, 0, 0), L
+    U = synth.gauge_field(L, seed=4321)
+    ref, _, _, st = oracle.propagator(U, L, oracle.BC_ANTIPERIODIC, o, e, 0.12, (0, 0, 0, 0), tol=1e-12)
+    assert st == 0
+    S = torch.from_numpy(ref).cuda()
+    got = torch.zeros(2 * L[0], dtype=torch.float64, device="cuda")
+    ddp.ddp_contract_static(ddp.DDP_CONTRACT_NUCLEON, L, o, e, S, got,
+                            stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    g = got.cpu().numpy()
+    want = oracle.nucleon(L, o, e, ref)
+    assert _rel(g[0::2] + 1j * g[1::2], want) <= CORR_TOL
+
+
+def _raw_static(ddp, kind, L, o, e, S_ptr, out_ptr):
+    """The C entry point itself, bypassing the binding's own checks."""
+    import ctypes
+    return ddp.lib().ddp_contract_static(int(kind), ddp._i4(L), ddp._i4(o), ddp._i4(e), S_ptr, None, 12,
+                                         ddp._i4((0, 0, 0, 0)), out_ptr, None)
+
+
 def test_static_rejects_sizes_beyond_its_array(ddp):
-    dummy = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    dummy = torch.zeros(16, dtype=torch.complex128, device="cuda")
     out = torch.zeros(2 * 132, dtype=torch.float64, device="cuda")
     L = (132, 32, 32, 32)   # 132 slices x 1024 nucleon chunks > the fixed array
-    with pytest.raises(ddp.DDPError) as ei:
-        ddp.ddp_contract_static(ddp.DDP_CONTRACT_NUCLEON, L, (0, 0, 0, 0), L, dummy, out)
-    assert ei.value.status == ddp.DDP_ERR_INVALID_ARG
+    rc = _raw_static(ddp, ddp.DDP_CONTRACT_NUCLEON, L, (0, 0, 0, 0), L, ddp._ptr(dummy), ddp._ptr(out))
+    assert rc == ddp.DDP_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+
+
+def test_static_rejects_host_and_short_buffers(ddp):
+    L = (8, 4, 4, 6)
+    n = int(np.prod(L))
+    S_dev = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
+    out_dev = torch.zeros(2 * L[0], dtype=torch.float64, device="cuda")
+    S_host = np.zeros((12, n, 4, 3), dtype=np.complex128)
+    out_host = np.zeros(2 * L[0])
+    # the C entry point refuses host memory before launching anything
+    for s_ptr, o_ptr in [(ddp._ptr(S_host), ddp._ptr(out_dev)), (ddp._ptr(S_dev), ddp._ptr(out_host))]:
+        assert _raw_static(ddp, ddp.DDP_CONTRACT_NUCLEON, L, (0, 0, 0, 0), L, s_ptr, o_ptr) == \
+            ddp.DDP_ERR_INVALID_ARG
+    # the binding refuses CPU tensors and tensors that are too short
+    for S, out in [(S_dev.cpu(), out_dev), (S_dev[:6], out_dev), (S_dev, out_dev[:4])]:
+        with pytest.raises(ddp.DDPError) as ei:
+            ddp.ddp_contract_static(ddp.DDP_CONTRACT_NUCLEON, L, (0, 0, 0, 0), L, S, out)
+        assert ei.value.status == ddp.DDP_ERR_INVALID_ARG
+    # an odd extent in the x3 direction is the geometry the library does not support
+    assert _raw_static(ddp, ddp.DDP_CONTRACT_NUCLEON, L, (0, 0, 0, 0), (8, 4, 4, 5), ddp._ptr(S_dev),
+                       ddp._ptr(out_dev)) == ddp.DDP_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
