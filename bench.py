@@ -278,8 +278,14 @@ def parity_block(ddp, torch, ctx, wl, U, cpu_cols):
     S_host = [o.cpu().numpy() for o in wl.outs]
     for i, (b, ref) in enumerate(zip(wl.bx[:2], cpu_cols)):
         got = S_host[i][0]
-        pi_ref = oracle.pion(L, b.origin, b.extent, ref[None])
-        pi_gpu = oracle.pion(L, b.origin, b.extent, got[None])
+        # the pion contraction of one column: the oracle's contraction with the other 11
+        # columns zero (sum over the column's own |psi|^2 per time slice)
+        one = np.zeros((12,) + got.shape, dtype=np.complex128)
+        one[0] = ref
+        pi_ref = oracle.pion(L, b.origin, b.extent, one)
+        one[0] = got
+        pi_gpu = oracle.pion(L, b.origin, b.extent, one)
+        del one
         out["columns"].append({"domain": list(b.extent), "column": 0, "rel_l2_error": _rel(got, ref),
                                "pion_rel_l2_error": _rel(pi_gpu, pi_ref)})
     for i, b in enumerate(wl.bx):

@@ -181,8 +181,15 @@ def series_term(L, small_o, small_e, S_small, big_o, big_e, S_big):
     return T
 
 
+def _twelve_columns(S, extent):
+    """The point-source contractions read exactly 12 columns of the box."""
+    if S.shape != (12, box_sites(extent), 4, 3):
+        raise ValueError(f"expected a 12-column propagator of shape (12, {box_sites(extent)}, 4, 3), got {S.shape}")
+
+
 def local_trace(L, origin, extent, S, src):
     S = _c(S)
+    _twelve_columns(S, extent)
     out = np.zeros(2)
     if lib().orc_contract_local_trace(_i4(L), _i4(origin), _i4(extent), _ptr(S), _i4(src), _ptr(out)):
         raise ValueError("source outside the box")
@@ -191,6 +198,7 @@ def local_trace(L, origin, extent, S, src):
 
 def pion(L, origin, extent, S):
     S = _c(S)
+    _twelve_columns(S, extent)
     out = np.zeros(int(L[0]))
     lib().orc_contract_pion(_i4(L), _i4(origin), _i4(extent), _ptr(S), _ptr(out))
     return out
@@ -198,6 +206,7 @@ def pion(L, origin, extent, S):
 
 def nucleon(L, origin, extent, S):
     S = _c(S)
+    _twelve_columns(S, extent)
     out = np.zeros(2 * int(L[0]))
     lib().orc_contract_nucleon(_i4(L), _i4(origin), _i4(extent), _ptr(S), _ptr(out))
     return out[0::2] + 1j * out[1::2]
