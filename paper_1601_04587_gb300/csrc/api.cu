@@ -55,11 +55,9 @@ void make_plan(const std::vector<Job> &jobs, int prec, const EngineParams &prm, 
     int TS = HOP_TS;
     plan.TS = TS;
     plan.CG = CG;
-    // pair kernels: the same number of columns per block, two per warp
-    plan.PG = std::min((CG + 1) / 2, HOP_MAX_PG);
     plan.items.clear();
-    int64_t fbase = 0, pbase = 0, qbase = 0;
-    int blk = 0, blkq = 0, solve = 0;
+    int64_t fbase = 0, pbase = 0;
+    int blk = 0, solve = 0;
     for (auto &j : jobs) {
         Item it;
         memset(&it, 0, sizeof(it));
@@ -78,31 +76,23 @@ void make_plan(const std::vector<Job> &jobs, int prec, const EngineParams &prm, 
         it.ntiles = (it.nh + TS - 1) / TS;
         it.ncol = j.ncol;
         it.ncg = (j.ncol + CG - 1) / CG;
-        it.npair = (j.ncol + 1) / 2;
-        it.npg = (it.npair + plan.PG - 1) / plan.PG;
         it.blk0 = blk;
-        it.blk0q = blkq;
         it.solve0 = solve;
         it.fbase = fbase;
-        it.qbase = qbase;
         it.pbase = pbase;
         it.kappa = j.kappa;
         it.links = j.g->links(prec);
         it.links64 = j.g->u64;
         it.gV = j.g->V;
         blk += it.ntiles * it.ncg;
-        blkq += it.ntiles * it.npg;
         solve += j.ncol;
         fbase += (int64_t)j.ncol * it.nh;
-        qbase += (int64_t)it.npair * it.nh;
         pbase += (int64_t)j.ncol * it.ntiles;
         plan.items.push_back(it);
     }
     plan.nblocks = blk;
-    plan.nqblocks = blkq;
     plan.nsolve = solve;
     plan.nfield = std::max<int64_t>(fbase, 1);
-    plan.nqfield = std::max<int64_t>(qbase, 1);
     plan.npart = std::max<int64_t>(pbase, 1);
 }
 

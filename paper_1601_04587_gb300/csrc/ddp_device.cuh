@@ -77,7 +77,6 @@ struct PF64 {
     static constexpr int NCH = 12;
     static constexpr bool SCALED = false;
     static constexpr int LCH = 9;
-    static constexpr int NSCALE = 0;
     static constexpr bool IS64 = true;
 };
 struct PF32 {
@@ -86,7 +85,6 @@ struct PF32 {
     static constexpr int NCH = 6;
     static constexpr bool SCALED = false;
     static constexpr int LCH = 3;
-    static constexpr int NSCALE = 0;
     static constexpr bool IS64 = false;
 };
 struct PF16 {
@@ -95,7 +93,6 @@ struct PF16 {
     static constexpr int NCH = 3;
     static constexpr bool SCALED = true;
     static constexpr int LCH = 3;
-    static constexpr int NSCALE = 1;
     static constexpr bool IS64 = false;
 };
 struct PBF16 {
@@ -104,7 +101,6 @@ struct PBF16 {
     static constexpr int NCH = 3;
     static constexpr bool SCALED = false;
     static constexpr int LCH = 3;
-    static constexpr int NSCALE = 0;
     static constexpr bool IS64 = false;
 };
 
@@ -351,11 +347,6 @@ struct Item {
     int solve0;      // first solve (column) index
     int64_t fbase;
     int64_t pbase;
-    // column-pair layout of the low-precision inner fields (ddp_pair.cuh)
-    int npair;       // ceil(ncol / 2)
-    int npg;         // ceil(npair / PG)
-    int blk0q;       // first block of the item in pair-kernel launches
-    int64_t qbase;   // first pair-site of the item
     double kappa;
     const void *links;    // links of the launch's storage precision
     const void *links64;  // FP64 links
@@ -366,7 +357,6 @@ struct Launch {
     const Item *items;
     int nitems;
     int TS, CG;          // sites per tile (multiple of 32), columns per block
-    int PG;              // column pairs per block of the pair kernels
 };
 
 // Locate the item owning block b (items sorted by blk0).

@@ -11,7 +11,7 @@
 #include <vector>
 
 #include "ddp.h"
-#include "ddp_pair.cuh"
+#include "ddp_kernels.cuh"
 
 namespace ddp {
 
@@ -158,23 +158,19 @@ ServerBase *make_server(ddp_ctx *ctx, int prec, uint64_t budget, int max_active,
 // Build the work table of a list of boxes (shared by the engine and apply).
 struct Plan {
     std::vector<Item> items;
-    int TS = 32, CG = 12, PG = 6;
-    int64_t nfield = 0;    // site-columns per parity field (per-column layout)
-    int64_t nqfield = 0;   // pair-sites per parity field (column-pair layout)
+    int TS = 32, CG = 12;
+    int64_t nfield = 0;    // site-columns per parity field
     int64_t npart = 0;     // partial slots
-    int nblocks = 0;       // blocks of the per-column kernels
-    int nqblocks = 0;      // blocks of the pair kernels
+    int nblocks = 0;
     int nsolve = 0;
 };
 
 void make_plan(const std::vector<Job> &jobs, int prec, const EngineParams &prm, Plan &plan);
 
-// Bytes of one parity field of nfield units (site-columns, or pair-sites for
-// the pair formats), rounded as the arena rounds.
 template <class P>
 inline size_t field_bytes(int64_t nfield) {
-    size_t b = (((size_t)nfield * sizeof(typename P::chunk) * P::NCH) + 255) & ~size_t(255);
-    if (P::SCALED) b += ((size_t)nfield * sizeof(float) * P::NSCALE + 255) & ~size_t(255);
+    size_t b = (size_t)nfield * sizeof(typename P::chunk) * P::NCH;
+    if (P::SCALED) b += ((size_t)nfield * sizeof(float) + 255) & ~size_t(255);
     return b + 256;
 }
 
@@ -183,7 +179,7 @@ inline FieldView carve_field(Arena &a, int64_t nfield) {
     FieldView f;
     f.stride = nfield;
     f.p = a.take((size_t)nfield * sizeof(typename P::chunk) * P::NCH);
-    f.scale = P::SCALED ? (float *)a.take((size_t)nfield * sizeof(float) * P::NSCALE) : nullptr;
+    f.scale = P::SCALED ? (float *)a.take((size_t)nfield * sizeof(float)) : nullptr;
     return f;
 }
 

@@ -29,34 +29,13 @@ inline void launch_hop(ddp_ctx *ctx, int nblocks, int threads, const HopArgs &a)
     k_hop<Q, EPI, DOT><<<nblocks, threads, 0, ctx->stream>>>(a);
 }
 
-// Layout of the inner-solver fields of a storage format: per column for FP64,
-// column pairs (ddp_pair.cuh) for the low-precision formats.
-template <class P>
-struct InnerOf {
-    using type = typename PairOf<P>::type;
-};
-template <>
-struct InnerOf<PF64> {
-    using type = PF64;
-};
-
-// The inner-loop stencil of storage format P on a launch of `plan`.
-template <class P, int EPI, int DOT>
-inline void launch_inner_hop(ddp_ctx *ctx, const Plan &plan, const HopArgs &a) {
-    if constexpr (P::IS64)
-        k_hop<PF64, EPI, DOT><<<plan.nblocks, plan.TS * plan.CG, 0, ctx->stream>>>(a);
-    else
-        k_qhop<typename PairOf<P>::type, EPI, DOT><<<plan.nqblocks, HOP_TS * plan.PG, 0, ctx->stream>>>(a);
-}
-
 template <class P>
 struct Engine {
-    using Q = typename InnerOf<P>::type;
     ddp_ctx *ctx;
     int prec;
     Plan plan;
-    FieldView be, bo, xe, xo, re64, ro64;      // FP64, per column
-    FieldView r, rh, p, v, s, t, xi, tmp, ro;  // storage format P, layout Q
+    FieldView be, bo, xe, xo, re64, ro64;      // FP64
+    FieldView r, rh, p, v, s, t, xi, tmp, ro;  // storage format P
     Partials A, B;
     Item *d_items = nullptr;
     SolveState *d_st = nullptr;
@@ -89,50 +68,27 @@ struct Engine {
         return a;
     }
 
-    // inner-loop stencil (storage format P)
-    template <int EPI, int DOT>
-    void ihop(const HopArgs &a) {
-        launch_inner_hop<P, EPI, DOT>(ctx, plan, a);
-        launches++;
-    }
-    // FP64 stencil on the FP64 per-column fields
-    template <int EPI, int DOT>
-    void hop64(const HopArgs &a) {
-        launch_hop<PF64, EPI, DOT>(ctx, plan.nblocks, threads, a);
+    template <class Q, int EPI, int DOT>
+    void hop(const HopArgs &a) {
+        launch_hop<Q, EPI, DOT>(ctx, plan.nblocks, threads, a);
         launches++;
     }
 
-    template <int OP>
+    template <class Q, int OP>
     void blas(Partials part, int skip = 1) {
-        if constexpr (P::IS64) {
-            BlasArgs a;
-            a.skip = skip;
-            a.L = L;
-            a.x = xi;
-            a.r = r;
-            a.rh = rh;
-            a.p = p;
-            a.v = v;
-            a.s = s;
-            a.t = t;
-            a.st = d_st;
-            a.part = part;
-            k_blas<PF64, OP><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
-        } else {
-            QBlasArgs a;
-            a.skip = skip;
-            a.L = L;
-            a.x = xi;
-            a.r = r;
-            a.rh = rh;
-            a.p = p;
-            a.v = v;
-            a.s = s;
-            a.t = t;
-            a.st = d_st;
-            a.part = part;
-            k_qblas<Q, OP><<<plan.nqblocks, HOP_TS * plan.PG, 0, ctx->stream>>>(a);
-        }
+        BlasArgs a;
+        a.skip = skip;
+        a.L = L;
+        a.x = xi;
+        a.r = r;
+        a.rh = rh;
+        a.p = p;
+        a.v = v;
+        a.s = s;
+        a.t = t;
+        a.st = d_st;
+        a.part = part;
+        k_blas<Q, OP><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
         launches++;
     }
 
@@ -162,43 +118,31 @@ struct Engine {
     }
 
     void conv(bool to_low, FieldView lo, FieldView hi) {
-        if constexpr (P::IS64) {
-            ConvArgs a;
-            a.L = L;
-            a.lo = lo;
-            a.hi = hi;
-            a.st = d_st;
-            if (to_low)
-                k_to_low<PF64><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
-            else
-                k_accum<PF64><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
-        } else {
-            QConvArgs a;
-            a.L = L;
-            a.lo = lo;
-            a.hi = hi;
-            a.st = d_st;
-            if (to_low)
-                k_to_pair<Q><<<plan.nqblocks, HOP_TS * plan.PG, 0, ctx->stream>>>(a);
-            else
-                k_accum_pair<Q><<<plan.nqblocks, HOP_TS * plan.PG, 0, ctx->stream>>>(a);
-        }
+        ConvArgs a;
+        a.L = L;
+        a.lo = lo;
+        a.hi = hi;
+        a.st = d_st;
+        if (to_low)
+            k_to_low<P><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
+        else
+            k_accum<P><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
         launches++;
     }
 
     // One BiCGStab iteration on the Schur complement (van der Vorst 1992).
     void iteration_body() {
         FieldView none = {nullptr, nullptr, 0};
-        ihop<EPI_PLAIN, DOT_NONE>(hop_args(1, p, tmp, none, none, none, A, 1));   // tmp = H_oe p
-        ihop<EPI_MHAT, DOT_RHAT>(hop_args(0, tmp, v, p, none, rh, A, 1));        // v = p - k^2 H_eo tmp
-        fin<FIN_ALPHA>();                                                         // alpha = rho / (rh, v)
-        blas<OP_S_UPDATE>(A);                                                     // s = r - alpha v
-        ihop<EPI_PLAIN, DOT_NONE>(hop_args(1, s, tmp, none, none, none, A, 1));   // tmp = H_oe s
-        ihop<EPI_MHAT, DOT_TS>(hop_args(0, tmp, t, s, none, none, A, 1));        // t = s - k^2 H_eo tmp
-        fin<FIN_OMEGA>();                                                         // omega = (t,s)/(t,t)
-        blas<OP_XR_UPDATE>(A);                                                    // x, r; (rh,r), (r,r)
-        fin<FIN_RHO>();                                                           // beta, convergence
-        blas<OP_P_UPDATE>(A);                                                     // p = r + beta (p - omega v)
+        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, p, tmp, none, none, none, A, 1));   // tmp = H_oe p
+        hop<P, EPI_MHAT, DOT_RHAT>(hop_args(0, tmp, v, p, none, rh, A, 1));        // v = p - k^2 H_eo tmp
+        fin<FIN_ALPHA>();                                                           // alpha = rho / (rh, v)
+        blas<P, OP_S_UPDATE>(A);                                                    // s = r - alpha v
+        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, s, tmp, none, none, none, A, 1));   // tmp = H_oe s
+        hop<P, EPI_MHAT, DOT_TS>(hop_args(0, tmp, t, s, none, none, A, 1));        // t = s - k^2 H_eo tmp
+        fin<FIN_OMEGA>();                                                           // omega = (t,s)/(t,t)
+        blas<P, OP_XR_UPDATE>(A);                                                   // x, r; (rh,r), (r,r)
+        fin<FIN_RHO>();                                                             // beta, convergence
+        blas<P, OP_P_UPDATE>(A);                                                    // p = r + beta (p - omega v)
     }
 
     int build_loop_graph() {
@@ -262,17 +206,14 @@ struct Engine {
 
     // ----------------------------------------------------------- building blocks
 
-    // cap: site-columns of the FP64 fields; qcap: units of the inner fields
-    // (pair-sites for the pair formats, site-columns for FP64).
-    static size_t bytes_needed(int64_t cap, int64_t qcap, int64_t npart, int nitems, int nsolve) {
-        return 6 * field_bytes<PF64>(cap) + 9 * field_bytes<Q>(qcap) +
+    static size_t bytes_needed(int64_t cap, int64_t npart, int nitems, int nsolve) {
+        return 6 * field_bytes<PF64>(cap) + 9 * field_bytes<P>(cap) +
                2 * ((size_t)npart * (sizeof(double2) + sizeof(double)) + 1024) + (size_t)nitems * sizeof(Item) +
                (size_t)nsolve * sizeof(SolveState) + sizeof(LoopCtl) + 8192;
     }
 
-    // FP64 fields get room for cap site-columns per parity (stride cap), the
-    // inner fields for qcap units.
-    void carve(Arena &a, int64_t cap, int64_t qcap, int64_t npart, int nitems, int nsolve) {
+    // Every field gets room for cap site-columns per parity (stride cap).
+    void carve(Arena &a, int64_t cap, int64_t npart, int nitems, int nsolve) {
         a.reset();
         be = carve_field<PF64>(a, cap);
         bo = carve_field<PF64>(a, cap);
@@ -280,15 +221,15 @@ struct Engine {
         xo = carve_field<PF64>(a, cap);
         re64 = carve_field<PF64>(a, cap);
         ro64 = carve_field<PF64>(a, cap);
-        r = carve_field<Q>(a, qcap);
-        rh = carve_field<Q>(a, qcap);
-        p = carve_field<Q>(a, qcap);
-        v = carve_field<Q>(a, qcap);
-        s = carve_field<Q>(a, qcap);
-        t = carve_field<Q>(a, qcap);
-        xi = carve_field<Q>(a, qcap);
-        tmp = carve_field<Q>(a, qcap);
-        ro = carve_field<Q>(a, qcap);
+        r = carve_field<P>(a, cap);
+        rh = carve_field<P>(a, cap);
+        p = carve_field<P>(a, cap);
+        v = carve_field<P>(a, cap);
+        s = carve_field<P>(a, cap);
+        t = carve_field<P>(a, cap);
+        xi = carve_field<P>(a, cap);
+        tmp = carve_field<P>(a, cap);
+        ro = carve_field<P>(a, cap);
         A.c = (double2 *)a.take(npart * sizeof(double2));
         A.n = (double *)a.take(npart * sizeof(double));
         B.c = (double2 *)a.take(npart * sizeof(double2));
@@ -305,7 +246,6 @@ struct Engine {
         L.nitems = (int)plan.items.size();
         L.TS = plan.TS;
         L.CG = plan.CG;
-        L.PG = plan.PG;
         threads = plan.TS * plan.CG;
         h_st = states;
         DDP_CUDA(ctx, cudaMemcpyAsync(d_items, plan.items.data(), plan.items.size() * sizeof(Item),
@@ -372,8 +312,8 @@ struct Engine {
     void residual(bool skip_hop) {
         FieldView none = {nullptr, nullptr, 0};
         if (!skip_hop) {
-            hop64<EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A, 2));
-            hop64<EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B, 2));
+            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A, 2));
+            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B, 2));
         }
         fin<FIN_RESID>();
     }
@@ -390,14 +330,14 @@ struct Engine {
         FieldView none = {nullptr, nullptr, 0};
         conv(true, s, r_is_eta ? be : re64);
         conv(true, ro, r_is_eta ? bo : ro64);
-        ihop<EPI_AXPY_K, DOT_NORM>(hop_args(0, ro, r, s, none, none, A));  // r = r'_e + k H_eo r'_o
-        blas<OP_INIT>(A, 0);
+        hop<P, EPI_AXPY_K, DOT_NORM>(hop_args(0, ro, r, s, none, none, A));  // r = r'_e + k H_eo r'_o
+        blas<P, OP_INIT>(A, 0);
         DDP_CUDA(ctx, cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), ctx->stream));
         fin<FIN_INIT>();
         DDP_CUDA(ctx, cudaGetLastError());
         int rc = run_inner();
         if (rc) return rc;
-        ihop<EPI_AXPY_K, DOT_NONE>(hop_args(1, xi, tmp, ro, none, none, A));  // e'_o = r'_o + k H_oe e'_e
+        hop<P, EPI_AXPY_K, DOT_NONE>(hop_args(1, xi, tmp, ro, none, none, A));  // e'_o = r'_o + k H_oe e'_e
         conv(false, xi, xe);
         conv(false, tmp, xo);
         return DDP_OK;
@@ -415,9 +355,8 @@ struct Engine {
     int run(std::vector<Job> &jobs, std::vector<JobInfo> &infos) {
         const EngineParams &prm = ctx->prm;
         make_plan(jobs, prec, prm, plan);
-        const int64_t qcap = P::IS64 ? plan.nfield : plan.nqfield;
-        DDP_CUDA(ctx, ctx->ws.reserve(bytes_needed(plan.nfield, qcap, plan.npart, (int)plan.items.size(), plan.nsolve)));
-        carve(ctx->ws, plan.nfield, qcap, plan.npart, (int)plan.items.size(), plan.nsolve);
+        DDP_CUDA(ctx, ctx->ws.reserve(bytes_needed(plan.nfield, plan.npart, (int)plan.items.size(), plan.nsolve)));
+        carve(ctx->ws, plan.nfield, plan.npart, (int)plan.items.size(), plan.nsolve);
         std::vector<SolveState> states(plan.nsolve);
         for (size_t i = 0; i < plan.items.size(); i++)
             for (int c = 0; c < plan.items[i].ncol; c++)
@@ -478,17 +417,16 @@ int solve_jobs(ddp_ctx *ctx, int prec, std::vector<Job> &jobs, std::vector<JobIn
 // out = D_Gamma psi with the stencil of storage format P (App. A, Sec. 2).
 template <class P>
 int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *out, int prec) {
-    using Q = typename InnerOf<P>::type;
     std::vector<Job> jobs(1, job);
     Plan plan;
     make_plan(jobs, prec, ctx->prm, plan);
-    const int64_t NF = P::IS64 ? plan.nfield : plan.nqfield;
-    size_t need = 4 * field_bytes<Q>(NF) + sizeof(Item) + 1024;
+    const int64_t NF = plan.nfield;
+    size_t need = 4 * field_bytes<P>(NF) + sizeof(Item) + 1024;
     DDP_CUDA(ctx, ctx->scratch.reserve(need));
     Arena &a = ctx->scratch;
     a.reset();
-    FieldView ie = carve_field<Q>(a, NF), io = carve_field<Q>(a, NF);
-    FieldView oe = carve_field<Q>(a, NF), oo = carve_field<Q>(a, NF);
+    FieldView ie = carve_field<P>(a, NF), io = carve_field<P>(a, NF);
+    FieldView oe = carve_field<P>(a, NF), oo = carve_field<P>(a, NF);
     Item *d_items = (Item *)a.take(sizeof(Item));
     cudaStream_t st = ctx->stream;
     DDP_CUDA(ctx, cudaMemcpyAsync(d_items, plan.items.data(), sizeof(Item), cudaMemcpyHostToDevice, st));
@@ -497,19 +435,14 @@ int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *ou
     pa.it = plan.items[0];
     pa.user = (const double2 *)psi;
     pa.uout = (double2 *)out;
-    const int64_t units = P::IS64 ? pa.it.ncol : pa.it.npair;
-    const int64_t nt = 2 * (int64_t)pa.it.nh * units;
-    const unsigned nb = (unsigned)((nt + 255) / 256);
-    if constexpr (P::IS64)
-        k_pack_low<PF64><<<nb, 256, 0, st>>>(pa, ie, io);
-    else
-        k_pack_pair<Q><<<nb, 256, 0, st>>>(pa, ie, io);
+    int64_t nt = 2 * (int64_t)pa.it.nh * pa.it.ncol;
+    unsigned nb = (unsigned)((nt + 255) / 256);
+    k_pack_low<P><<<nb, 256, 0, st>>>(pa, ie, io);
     Launch L;
     L.items = d_items;
     L.nitems = 1;
     L.TS = plan.TS;
     L.CG = plan.CG;
-    L.PG = plan.PG;
     FieldView none = {nullptr, nullptr, 0};
     HopArgs h;
     h.st = nullptr;
@@ -523,16 +456,13 @@ int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *ou
     h.in = io;
     h.out = oe;
     h.v1 = ie;
-    launch_inner_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan, h);
+    launch_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
     h.p = 1;
     h.in = ie;
     h.out = oo;
     h.v1 = io;
-    launch_inner_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan, h);
-    if constexpr (P::IS64)
-        k_unpack_low<PF64><<<nb, 256, 0, st>>>(pa, oe, oo);
-    else
-        k_unpack_pair<Q><<<nb, 256, 0, st>>>(pa, oe, oo);
+    launch_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+    k_unpack_low<P><<<nb, 256, 0, st>>>(pa, oe, oo);
     ctx->launches += 4;
     DDP_CUDA(ctx, cudaGetLastError());
     return DDP_OK;
@@ -618,38 +548,36 @@ int hop_power_impl(ddp_ctx *ctx, const Job &job, int p, const double *psi, doubl
 // site once for all columns.
 template <class P>
 int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int kernel, int iters, float *ms, double *bytes) {
-    using Q = typename InnerOf<P>::type;
     std::vector<Job> jobs(1, job);
     Plan plan;
     make_plan(jobs, prec, ctx->prm, plan);
-    const int64_t NF = P::IS64 ? plan.nfield : plan.nqfield;
-    size_t need = 4 * field_bytes<Q>(NF) + 2 * ((size_t)plan.npart * 24 + 1024) + sizeof(Item) + 1024;
+    const int64_t NF = plan.nfield;
+    size_t need = 4 * field_bytes<P>(NF) + 2 * ((size_t)plan.npart * 24 + 1024) + sizeof(Item) + 1024;
     DDP_CUDA(ctx, ctx->scratch.reserve(need));
     Arena &a = ctx->scratch;
     a.reset();
-    FieldView in = carve_field<Q>(a, NF), v1 = carve_field<Q>(a, NF), rhv = carve_field<Q>(a, NF),
-              out = carve_field<Q>(a, NF);
+    FieldView in = carve_field<P>(a, NF), v1 = carve_field<P>(a, NF), rhv = carve_field<P>(a, NF),
+              out = carve_field<P>(a, NF);
     Partials A;
     A.c = (double2 *)a.take(plan.npart * sizeof(double2));
     A.n = (double *)a.take(plan.npart * sizeof(double));
     Item *d_items = (Item *)a.take(sizeof(Item));
     cudaStream_t st = ctx->stream;
     DDP_CUDA(ctx, cudaMemcpyAsync(d_items, plan.items.data(), sizeof(Item), cudaMemcpyHostToDevice, st));
-    const size_t fb = (size_t)NF * sizeof(typename Q::chunk) * Q::NCH;
+    size_t fb = (size_t)NF * sizeof(typename P::chunk) * P::NCH;
     DDP_CUDA(ctx, cudaMemsetAsync(in.p, 0, fb, st));
     DDP_CUDA(ctx, cudaMemsetAsync(v1.p, 0, fb, st));
     DDP_CUDA(ctx, cudaMemsetAsync(rhv.p, 0, fb, st));
-    if (Q::SCALED) {
-        DDP_CUDA(ctx, cudaMemsetAsync(in.scale, 0, NF * sizeof(float) * Q::NSCALE, st));
-        DDP_CUDA(ctx, cudaMemsetAsync(v1.scale, 0, NF * sizeof(float) * Q::NSCALE, st));
-        DDP_CUDA(ctx, cudaMemsetAsync(rhv.scale, 0, NF * sizeof(float) * Q::NSCALE, st));
+    if (P::SCALED) {
+        DDP_CUDA(ctx, cudaMemsetAsync(in.scale, 0, NF * sizeof(float), st));
+        DDP_CUDA(ctx, cudaMemsetAsync(v1.scale, 0, NF * sizeof(float), st));
+        DDP_CUDA(ctx, cudaMemsetAsync(rhv.scale, 0, NF * sizeof(float), st));
     }
     Launch L;
     L.items = d_items;
     L.nitems = 1;
     L.TS = plan.TS;
     L.CG = plan.CG;
-    L.PG = plan.PG;
     HopArgs h;
     FieldView none = {nullptr, nullptr, 0};
     h.st = nullptr;
@@ -664,11 +592,11 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int kernel, int iters,
     h.part = A;
     auto launch = [&]() {
         if (kernel == DDP_HOP_PLAIN)
-            launch_inner_hop<P, EPI_PLAIN, DOT_NONE>(ctx, plan, h);
+            launch_hop<P, EPI_PLAIN, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
         else if (kernel == DDP_HOP_SCHUR_RHAT)
-            launch_inner_hop<P, EPI_MHAT, DOT_RHAT>(ctx, plan, h);
+            launch_hop<P, EPI_MHAT, DOT_RHAT>(ctx, plan.nblocks, plan.TS * plan.CG, h);
         else
-            launch_inner_hop<P, EPI_MHAT, DOT_TS>(ctx, plan, h);
+            launch_hop<P, EPI_MHAT, DOT_TS>(ctx, plan.nblocks, plan.TS * plan.CG, h);
     };
     cudaEvent_t e0, e1;
     DDP_CUDA(ctx, cudaEventCreate(&e0));
@@ -685,7 +613,6 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int kernel, int iters,
     DDP_CUDA(ctx, cudaGetLastError());
     ctx->launches += 3 + iters;
     *ms = t / iters;
-    // algorithmic bytes: independent of the layout (per site-column of one column)
     const double site_cols = (double)plan.items[0].nh * job.ncol;
     const double spinor = (double)sizeof(typename P::chunk) * P::NCH + (P::SCALED ? 4.0 : 0.0);
     const double link = P::IS64 ? 144.0 : (std::is_same<P, PF32>::value ? 48.0 : 24.0);

@@ -52,26 +52,19 @@ struct Server : ServerBase {
         eng.prec = precision;
         max_active = maxact;
         nsolve_cap = MAX_NCOL * maxact;
-        // bytes per site-column of capacity (fields) plus the per-tile partials; the
-        // inner fields of the pair formats hold two site-columns per unit
-        double per = (double)Engine<P>::bytes_needed(1 << 20, qcap_of(1 << 20), 0, 0, 0) / (1 << 20) +
-                     2.0 * 24.0 / 32.0;
+        // bytes per site-column of capacity (fields) plus the per-tile partials
+        double per = (double)Engine<P>::bytes_needed(1 << 20, 0, 0, 0) / (1 << 20) + 2.0 * 24.0 / 32.0;
         cap = (int64_t)((double)budget / per);
-        cap = (cap / 64) * 64;
+        cap = (cap / 32) * 32;
         if (cap < 1024) return DDP_ERR_OOM;
         npart_cap = cap / 32 + (int64_t)nsolve_cap + 64;
-        size_t need = Engine<P>::bytes_needed(cap, qcap_of(cap), npart_cap, maxact, nsolve_cap);
+        size_t need = Engine<P>::bytes_needed(cap, npart_cap, maxact, nsolve_cap);
         cudaError_t e = arena.reserve(need);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "serving arena");
-        eng.carve(arena, cap, qcap_of(cap), npart_cap, maxact, nsolve_cap);
+        eng.carve(arena, cap, npart_cap, maxact, nsolve_cap);
         free_[0] = cap;
         return DDP_OK;
     }
-
-    // Ranges are allocated in site-columns of the FP64 fields with an even number
-    // of columns per request, so that offset / 2 is the request's first
-    // pair-site in the inner fields of the pair formats.
-    static int64_t qcap_of(int64_t cap) { return P::IS64 ? cap : cap / 2; }
 
     bool alloc(int64_t len, int64_t *off) {
         for (auto it = free_.begin(); it != free_.end(); ++it) {
@@ -106,7 +99,7 @@ struct Server : ServerBase {
     int submit(const Job &job, uint64_t ticket) override {
         if (job.ncol > MAX_NCOL) return DDP_ERR_UNSUPPORTED;
         int64_t nh = (int64_t)job.e[0] * job.e[1] * job.e[2] * job.e[3] / 2;
-        int64_t len = nh * (P::IS64 ? job.ncol : 2 * ((job.ncol + 1) / 2));
+        int64_t len = nh * job.ncol;
         if (len > cap) return DDP_ERR_OOM;  // can never fit this server
         if ((int)active.size() >= max_active) return DDP_ERR_BUSY;
         int64_t off;
@@ -135,7 +128,6 @@ struct Server : ServerBase {
             Req &r = reqs[active[i]];
             Item &it = eng.plan.items[i];
             it.fbase = r.off;
-            it.qbase = P::IS64 ? r.off : r.off / 2;
             for (int c = 0; c < it.ncol; c++) {
                 SolveState S = r.fresh ? eng.fresh_state((int)i, c, r.job.tol) : r.st[c];
                 S.item = (int)i;
