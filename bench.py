@@ -135,6 +135,9 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- GPU arm
 
+CONTRACT_MASK = 0b1101   # local trace (kind 0), nucleon (kind 2), pion (kind 3)
+
+
 class Workload:
     def __init__(self, ddp, torch, ctx, precision, U):
         self.ddp, self.torch, self.ctx, self.prec = ddp, torch, ctx, precision
@@ -142,28 +145,24 @@ class Workload:
         self.bx = boxes()
         self.outs = [torch.zeros((12, b.n_sites, 4, 3), dtype=torch.complex128, device="cuda") for b in self.bx]
         self.terms = [torch.zeros_like(o) for o in self.outs[1:]]
-        self.C = torch.zeros((len(self.bx), 2, 2 * L[0]), dtype=torch.float64, device="cuda")
-        self.trace = torch.zeros((len(self.bx), 2), dtype=torch.float64, device="cuda")
+        # [domain][contraction kind][2 L0]: kind 0 local trace (first 2 entries), 2 nucleon, 3 pion
+        self.C = torch.zeros((len(self.bx), 4, 2 * L[0]), dtype=torch.float64, device="cuda")
         self.infos = None
 
     def step(self, host=None):
-        """One pass of the hot path.  host: pinned host buffers for the e2e variant."""
+        """One pass of the hot path: gauge field in, the four nested propagators, their
+        series terms and contractions out, in one library call.  host: pinned host
+        buffers for the end-to-end variant (the gauge field is uploaded, every result
+        downloaded, nothing uploaded twice)."""
         ddp, ctx = self.ddp, self.ctx
         U = self.U_dev if host is None else host["U"]
         outs = self.outs if host is None else host["S"]
         terms = self.terms if host is None else host["T"]
         C = self.C if host is None else host["C"]
-        tr = self.trace if host is None else host["tr"]
         gid = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
         dids = [ddp.ddp_set_domain(ctx, gid, b.origin, b.extent) for b in self.bx]
-        reqs = [ddp.make_req(d, KAPPA, SRC, TOL, o) for d, o in zip(dids, outs)]
-        rc, self.infos = ddp.ddp_solve_batch(ctx, reqs, self.prec)
-        for i in range(1, len(dids)):
-            ddp.ddp_series_terms(ctx, dids[i - 1], outs[i - 1], dids[i], outs[i], terms[i - 1], 12)
-        for i, d in enumerate(dids):
-            ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_NUCLEON, d, outs[i], C[i, 0])
-            ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PION, d, outs[i], C[i, 1])
-            ddp.ddp_contract(ctx, ddp.DDP_CONTRACT_PSEUDO_LOCAL, d, outs[i], tr[i], src=SRC)
+        rc, self.infos = ddp.ddp_propagator_series(ctx, dids, KAPPA, SRC, TOL, self.prec, S_out=outs, T_out=terms,
+                                                   contract_mask=CONTRACT_MASK, C_out=C)
         for d in dids:
             ddp.ddp_free_domain(ctx, d)
         ddp.ddp_free_gauge(ctx, gid)
@@ -174,17 +173,11 @@ class Workload:
         h = {"U": t.from_numpy(np.ascontiguousarray(self.U_dev.cpu().numpy())).pin_memory(),
              "S": [t.zeros(o.shape, dtype=o.dtype).pin_memory() for o in self.outs],
              "T": [t.zeros(o.shape, dtype=o.dtype).pin_memory() for o in self.terms],
-             "C": t.zeros(self.C.shape, dtype=t.float64).pin_memory(),
-             "tr": t.zeros(self.trace.shape, dtype=t.float64).pin_memory()}
+             "C": t.zeros(self.C.shape, dtype=t.float64).pin_memory()}
         nb = lambda x: x.numel() * x.element_size()  # noqa: E731
-        S = sum(nb(x) for x in h["S"])
-        T = sum(nb(x) for x in h["T"])
-        # H2D: gauge field, both propagators of every series term, the propagator of the
-        # nucleon and of the pion contraction, and the source-site rows (12 columns x 12
-        # complex) the local trace reads
-        h2d = (nb(h["U"]) + sum(nb(h["S"][i - 1]) + nb(h["S"][i]) for i in range(1, 4)) + 2 * S
-               + len(h["S"]) * 12 * 12 * 16)
-        d2h = S + T + nb(h["C"]) + nb(h["tr"])
+        # H2D: the gauge field only; D2H: the propagators, the series terms and the correlators
+        h2d = nb(h["U"])
+        d2h = sum(nb(x) for x in h["S"]) + sum(nb(x) for x in h["T"]) + nb(h["C"])
         return h, h2d, d2h
 
 
@@ -301,10 +294,10 @@ def parity_block(ddp, torch, ctx, wl, U, cpu_cols):
         nuc = oracle.nucleon(L, b.origin, b.extent, S)
         pio = oracle.pion(L, b.origin, b.extent, S)
         ltr = oracle.local_trace(L, b.origin, b.extent, S, SRC)
-        tr = wl.trace[i].cpu().numpy()
+        tr = C[0]
         out["correlators"].append({"domain": list(b.extent),
-                                   "nucleon_rel_l2_error": _rel(C[0, 0::2] + 1j * C[0, 1::2], nuc),
-                                   "pion_rel_l2_error": _rel(C[1, 0::2], pio),
+                                   "nucleon_rel_l2_error": _rel(C[2, 0::2] + 1j * C[2, 1::2], nuc),
+                                   "pion_rel_l2_error": _rel(C[3, 0::2], pio),
                                    "local_trace_rel_error": abs(complex(tr[0], tr[1]) - ltr) / abs(ltr)})
     out["max_column_rel_l2_error"] = max(c["rel_l2_error"] for c in out["columns"])
     out["max_oracle_rel_residual"] = max(p["oracle_max_rel_residual"] for p in out["propagators"])

@@ -210,6 +210,30 @@ int ddp_series_terms(ddp_ctx *ctx, int domain_small, const double *S_small, int 
  * DDP_ERR_INVALID_ARG for ncol < 1 or domains of different gauge fields. */
 int ddp_boundary_source(ddp_ctx *ctx, int domain_from, const double *psi, int domain_to, double *sigma, int ncol);
 
+/* The point-source propagators S^(i) = D_{Gamma_i}^{-1}(., x) of nested domains
+ * Gamma_0 in Gamma_1 in ... in Gamma_{n-1} (Sec. 2, Eq. diric), solved in one
+ * batch, the terms of their series T^(i) = S^(i) - E S^(i-1) (Sec. 1, Eq. Dseries)
+ * and the point-source contractions of every S^(i) (Sec. 3 Eq. W0, Sec. 4), in one
+ * call that keeps every intermediate on the device.
+ *  - domain_ids: n domains of one gauge field, each inside the next (else
+ *    DDP_ERR_INVALID_ARG); src must lie in Gamma_0.
+ *  - S_out: n pointers (or NULL), entry i receives S^(i) as ddp_solve_propagator
+ *    writes it, or is NULL when S^(i) is not wanted.  T_out: n-1 pointers (or
+ *    NULL), entry i-1 receives T^(i) in the layout of ddp_series_terms.
+ *  - contract_mask: bit k set for ddp_contract_kind k among PSEUDO_LOCAL, NUCLEON,
+ *    PION (PSEUDO_NOISE needs sources: DDP_ERR_INVALID_ARG).  C_out holds
+ *    n x 4 x 2*L0 doubles: the result of kind k for domain i at offset
+ *    (4 i + k) 2 L0, in the layout of ddp_contract; other entries are untouched.
+ *  - Outputs may be host or device memory (detected per pointer); host outputs
+ *    are copied down on a second stream while the later kernels run, and
+ *    nothing the call computed is uploaded again.  Device-resident copies live
+ *    in the context until its next call of this function.
+ *  - Returns DDP_ERR_NOT_CONVERGED (with every output written) when a solve missed
+ *    tol; infos: n entries or NULL.  csw != 0: DDP_ERR_UNSUPPORTED. */
+int ddp_propagator_series(ddp_ctx *ctx, int n, const int *domain_ids, double kappa, double csw, const int src[4],
+                          double tol, int precision, double *const *S_out, double *const *T_out, int contract_mask,
+                          double *C_out, ddp_solve_info *infos);
+
 /* Wick contractions of a solved propagator on a domain.
  *  PSEUDO_LOCAL: S = 12 point-source columns, src = the source; C_out[2] = tr{g5 S(x,x)}.
  *  PSEUDO_NOISE: S = psi_c = D_Gamma^{-1} eta_c, eta = the ncol sources;

@@ -95,6 +95,8 @@ def lib():
             "ddp_contract_static": ([i, i4, i4, i4, vp, vp, i, i4, vp, vp], i),
             "ddp_factorized_correlator": ([vp, vp, i, vp, i, i, d, vp], i),
             "ddp_autotune": ([vp, i, d, i, i, i, i4, ctypes.POINTER(ctypes.c_float)], i),
+            "ddp_propagator_series": ([vp, i, i4, d, d, i4, d, i, ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp,
+                                       ctypes.POINTER(ddp_solve_info)], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -253,6 +255,24 @@ def ddp_series_terms(ctx, domain_small, S_small, domain_big, S_big, T_out, ncol=
 def ddp_contract(ctx, kind, domain_id, S, C_out, eta=None, ncol=12, src=(0, 0, 0, 0)):
     return _check(ctx, lib().ddp_contract(ctx, int(kind), int(domain_id), _ptr(S), _ptr(eta), int(ncol), _i4(src),
                                           _ptr(C_out)), "ddp_contract")
+
+
+def ddp_propagator_series(ctx, domain_ids, kappa, src, tol, precision, S_out=None, T_out=None, contract_mask=0,
+                          C_out=None, csw=0.0):
+    """Nested-domain propagators, their series terms and contractions in one call
+    (include/ddp.h).  S_out: list of n arrays or None entries; T_out: list of n-1;
+    C_out: n x 4 x 2*L0 doubles.  Returns (status, infos)."""
+    n = len(domain_ids)
+    ids = (ctypes.c_int * n)(*[int(d) for d in domain_ids])
+    sp = (ctypes.c_void_p * n)(*[(_ptr(x).value if x is not None else None) for x in (S_out or [None] * n)])
+    tl = T_out or [None] * max(n - 1, 1)
+    tp = (ctypes.c_void_p * len(tl))(*[(_ptr(x).value if x is not None else None) for x in tl])
+    infos = (ddp_solve_info * n)()
+    rc = lib().ddp_propagator_series(ctx, n, ids, float(kappa), float(csw), _i4(src), float(tol), int(precision),
+                                     sp if S_out is not None else None, tp if T_out is not None else None,
+                                     int(contract_mask), _ptr(C_out), infos)
+    _check(ctx, rc, "ddp_propagator_series", allow=(DDP_ERR_NOT_CONVERGED,))
+    return rc, list(infos)
 
 
 def ddp_factorized_correlator(ctx, T_A, nvar_A, T_B, nvar_B, L0, spatial_volume, C_out):

@@ -515,6 +515,10 @@ int ddp_destroy(ddp_ctx *ctx) {
     }
     cudaEventDestroy(ctx->ev_in);
     cudaEventDestroy(ctx->ev_out);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
     cudaStreamDestroy(ctx->stream);
     delete ctx;
     return DDP_OK;
@@ -965,6 +969,130 @@ int ddp_series_terms(ddp_ctx *ctx, int domain_small, const double *S_small, int 
     if ((rc = t.copy_out())) return rc;
     DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return DDP_OK;
+}
+
+// Point-source propagators of nested domains Gamma_0 in ... in Gamma_{n-1} solved
+// together, the series terms S^(i) - E S^(i-1) (Eq. Dseries) and the contractions
+// of every S^(i), with all intermediate results kept on the device: outputs in
+// host memory are only ever downloaded, on a second stream while later kernels
+// run, never uploaded again.
+int ddp_propagator_series(ddp_ctx *ctx, int n, const int *domain_ids, double kappa, double csw, const int src[4],
+                          double tol, int precision, double *const *S_out, double *const *T_out, int contract_mask,
+                          double *C_out, ddp_solve_info *infos) {
+    if (!ctx || n < 1 || !domain_ids || !src) return DDP_ERR_INVALID_ARG;
+    const int allowed = (1 << DDP_CONTRACT_PSEUDO_LOCAL) | (1 << DDP_CONTRACT_NUCLEON) | (1 << DDP_CONTRACT_PION);
+    if (contract_mask & ~allowed) return DDP_ERR_INVALID_ARG;
+    if (contract_mask && !C_out) return DDP_ERR_INVALID_ARG;
+    if (csw != 0.0) return DDP_ERR_UNSUPPORTED;
+    std::vector<const DomainDev *> dom(n);
+    std::vector<const GaugeDev *> gau(n);
+    for (int i = 0; i < n; i++) {
+        int rc = find_domain(ctx, domain_ids[i], &dom[i], &gau[i]);
+        if (rc) return rc;
+        if (gau[i] != gau[0]) return DDP_ERR_INVALID_ARG;
+    }
+    const GaugeDev &g = *gau[0];
+    // nesting: every site of domain i-1 lies in domain i
+    for (int i = 1; i < n; i++)
+        for (int m = 0; m < 4; m++) {
+            if (dom[i]->e[m] == g.L[m]) continue;
+            int d0 = ((dom[i - 1]->o[m] - dom[i]->o[m]) % g.L[m] + g.L[m]) % g.L[m];
+            if (dom[i - 1]->e[m] > dom[i]->e[m] || d0 + dom[i - 1]->e[m] > dom[i]->e[m]) return DDP_ERR_INVALID_ARG;
+        }
+    DeviceGuard dg(ctx->device);
+    StreamJoin sj(ctx);
+    const int L0 = g.L[0];
+    // device buffers: the caller's where they are device memory, else the results arena
+    std::vector<size_t> sb(n);
+    size_t need = 0;
+    for (int i = 0; i < n; i++) {
+        sb[i] = (size_t)12 * dom[i]->n * 12 * sizeof(double2);
+        if (!(S_out && S_out[i] && is_device_ptr(S_out[i]))) need += sb[i] + 256;
+        if (i > 0 && T_out && T_out[i - 1] && !is_device_ptr(T_out[i - 1])) need += sb[i] + 256;
+    }
+    const size_t cbytes = (size_t)n * 4 * 2 * L0 * sizeof(double);
+    const bool c_dev = contract_mask && is_device_ptr(C_out);
+    if (contract_mask && !c_dev) need += cbytes + 256;
+    DDP_CUDA(ctx, ctx->results.reserve(need + 1024));
+    Arena &ar = ctx->results;
+    ar.reset();
+    std::vector<double *> dS(n), dT(n, nullptr);
+    std::vector<char> s_host(n, 0), t_host(n, 0);
+    for (int i = 0; i < n; i++) {
+        if (S_out && S_out[i] && is_device_ptr(S_out[i])) {
+            dS[i] = S_out[i];
+        } else {
+            dS[i] = (double *)ar.take(sb[i]);
+            s_host[i] = S_out && S_out[i];
+        }
+        if (i > 0 && T_out && T_out[i - 1]) {
+            if (is_device_ptr(T_out[i - 1])) {
+                dT[i] = T_out[i - 1];
+            } else {
+                dT[i] = (double *)ar.take(sb[i]);
+                t_host[i] = 1;
+            }
+        }
+    }
+    double *dC = nullptr;
+    if (contract_mask) dC = c_dev ? C_out : (double *)ar.take(cbytes);
+    std::vector<ddp_solve_req> reqs(n);
+    for (int i = 0; i < n; i++) {
+        ddp_solve_req &r = reqs[i];
+        memset(&r, 0, sizeof(r));
+        r.domain_id = domain_ids[i];
+        r.kappa = kappa;
+        r.csw = csw;
+        memcpy(r.src, src, sizeof(r.src));
+        r.ncol = 12;
+        r.tol = tol;
+        r.out = dS[i];
+    }
+    int worst = run_solves(ctx, reqs.data(), n, precision, infos);
+    if (worst != DDP_OK && worst != DDP_ERR_NOT_CONVERGED) return worst;
+    if (!ctx->copy_stream) DDP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = ctx->copy_stream;
+    cudaEvent_t ev;
+    DDP_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    auto download = [&](void *dst, const void *srcp, size_t bytes) -> int {
+        DDP_CUDA(ctx, cudaEventRecord(ev, ctx->stream));
+        DDP_CUDA(ctx, cudaStreamWaitEvent(cs, ev, 0));
+        DDP_CUDA(ctx, cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyDeviceToHost, cs));
+        return DDP_OK;
+    };
+    int rc = DDP_OK;
+    for (int i = 0; i < n && !rc; i++)
+        if (s_host[i]) rc = download(S_out[i], dS[i], sb[i]);
+    for (int i = 1; i < n && !rc; i++) {
+        if (!dT[i]) continue;
+        SeriesArgs sa;
+        sa.big = item_of(g, *dom[i], 12, DDP_PREC_FP64);
+        sa.small = item_of(g, *dom[i - 1], 12, DDP_PREC_FP64);
+        sa.Sb = (const double2 *)dS[i];
+        sa.Ss = (const double2 *)dS[i - 1];
+        sa.T = (double2 *)dT[i];
+        sa.ncol = 12;
+        const int64_t nt = (int64_t)12 * dom[i]->n;
+        k_series<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(sa);
+        ctx->launches++;
+        if (cudaPeekAtLastError() != cudaSuccess) {
+            rc = set_cuda_error(ctx, cudaGetLastError(), "series term");
+            break;
+        }
+        if (t_host[i]) rc = download(T_out[i - 1], dT[i], sb[i]);
+    }
+    for (int i = 0; i < n && !rc && contract_mask; i++)
+        for (int k = 0; k < 4 && !rc; k++) {
+            if (!((contract_mask >> k) & 1)) continue;
+            rc = ddp_contract(ctx, k, domain_ids[i], dS[i], nullptr, 12, src, dC + ((size_t)i * 4 + k) * 2 * L0);
+        }
+    if (!rc && contract_mask && !c_dev) rc = download(C_out, dC, cbytes);
+    cudaError_t e1 = cudaStreamSynchronize(cs), e2 = cudaStreamSynchronize(ctx->stream);
+    cudaEventDestroy(ev);
+    if (rc) return rc;
+    if (e1 != cudaSuccess) return set_cuda_error(ctx, e1, "device to host copies");
+    if (e2 != cudaSuccess) return set_cuda_error(ctx, e2, "synchronize");
+    return worst;
 }
 
 // Boundary coupling of two domains of one gauge field (Eq. blkdec), the source of

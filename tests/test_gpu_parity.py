@@ -488,3 +488,73 @@ def test_zero_source_and_bad_kappa(ddp, ctx, field):
         assert ei.value.status == ddp.DDP_ERR_INVALID_ARG
     with pytest.raises(ddp.DDPError):
         ddp.ddp_solve_sources(ctx, did, 0.124, 0.0, eta, 3, 0.0, 1, out)      # tol must be positive
+
+
+# ------------------------------------------------- nested propagators in one call
+
+@pytest.mark.parametrize("where", ["device", "pinned", "numpy"])
+def test_propagator_series_matches_separate_calls(ddp, ctx, field, where):
+    """ddp_propagator_series gives the same bits as ddp_solve_batch + ddp_series_terms +
+    ddp_contract on the same nested domains, whether its outputs are device memory,
+    pinned host memory or plain numpy arrays; the propagators also match the oracle."""
+    U, gid = field
+    src, kappa = (7, 1, 2, 3), 0.124
+    boxes = [((6, 0, 0, 0), (4, 4, 4, 6)), ((5, 0, 0, 0), (6, 4, 4, 6)), ((0, 0, 0, 0), LAT)]
+    dids = [ddp.ddp_set_domain(ctx, gid, *b) for b in boxes]
+    shapes = [(12, int(np.prod(b[1])), 4, 3) for b in boxes]
+    prec = ddp.DDP_PREC_MIXED_FP32
+    # separate calls on device buffers
+    S = [torch.zeros(sh, dtype=torch.complex128, device="cuda") for sh in shapes]
+    reqs = [ddp.make_req(d, kappa, src, 1e-10, o) for d, o in zip(dids, S)]
+    rc, _ = ddp.ddp_solve_batch(ctx, reqs, prec)
+    assert rc == ddp.DDP_OK
+    T = [torch.zeros(sh, dtype=torch.complex128, device="cuda") for sh in shapes[1:]]
+    for i in range(1, 3):
+        ddp.ddp_series_terms(ctx, dids[i - 1], S[i - 1], dids[i], S[i], T[i - 1], 12)
+    mask = (1 << ddp.DDP_CONTRACT_PSEUDO_LOCAL) | (1 << ddp.DDP_CONTRACT_NUCLEON) | (1 << ddp.DDP_CONTRACT_PION)
+    C = np.zeros((3, 4, 2 * LAT[0]))
+    for i, d in enumerate(dids):
+        for k in (ddp.DDP_CONTRACT_PSEUDO_LOCAL, ddp.DDP_CONTRACT_NUCLEON, ddp.DDP_CONTRACT_PION):
+            out = np.zeros(2 * LAT[0])
+            ddp.ddp_contract(ctx, k, d, S[i], out, src=src)
+            C[i, k] = out
+    # one call
+    if where == "device":
+        mk = lambda sh: torch.zeros(sh, dtype=torch.complex128, device="cuda")  # noqa: E731
+        Cg = torch.zeros((3, 4, 2 * LAT[0]), dtype=torch.float64, device="cuda")
+    elif where == "pinned":
+        mk = lambda sh: torch.zeros(sh, dtype=torch.complex128).pin_memory()  # noqa: E731
+        Cg = torch.zeros((3, 4, 2 * LAT[0]), dtype=torch.float64).pin_memory()
+    else:
+        mk = lambda sh: np.zeros(sh, dtype=np.complex128)  # noqa: E731
+        Cg = np.zeros((3, 4, 2 * LAT[0]))
+    S2 = [mk(sh) for sh in shapes]
+    T2 = [mk(sh) for sh in shapes[1:]]
+    rc, infos = ddp.ddp_propagator_series(ctx, dids, kappa, src, 1e-10, prec, S_out=S2, T_out=T2,
+                                          contract_mask=mask, C_out=Cg)
+    assert rc == ddp.DDP_OK
+    host = lambda x: x.cpu().numpy() if hasattr(x, "cpu") else x  # noqa: E731
+    for a, b in zip(S2, S):
+        assert np.array_equal(host(a), b.cpu().numpy())
+    for a, b in zip(T2, T):
+        assert np.array_equal(host(a), b.cpu().numpy())
+    Cg = host(Cg)
+    for i in range(3):
+        for k in (ddp.DDP_CONTRACT_PSEUDO_LOCAL, ddp.DDP_CONTRACT_NUCLEON, ddp.DDP_CONTRACT_PION):
+            n = 2 if k == ddp.DDP_CONTRACT_PSEUDO_LOCAL else 2 * LAT[0]
+            assert np.array_equal(Cg[i, k, :n], C[i, k, :n]), (i, k)
+    ref, *_ = oracle.propagator(U, LAT, AP, *boxes[0], kappa, src)
+    assert max(_col_errors(host(S2[0]), ref)) < 1e-8
+    for d in dids:
+        ddp.ddp_free_domain(ctx, d)
+
+
+def test_propagator_series_rejects_non_nested(ddp, ctx, field):
+    U, gid = field
+    a = ddp.ddp_set_domain(ctx, gid, (6, 0, 0, 0), (4, 4, 4, 6))
+    b = ddp.ddp_set_domain(ctx, gid, (0, 0, 0, 0), (4, 4, 4, 6))
+    with pytest.raises(ddp.DDPError) as ei:
+        ddp.ddp_propagator_series(ctx, [a, b], 0.124, (7, 0, 0, 0), 1e-10, ddp.DDP_PREC_MIXED_FP32)
+    assert ei.value.status == ddp.DDP_ERR_INVALID_ARG
+    ddp.ddp_free_domain(ctx, a)
+    ddp.ddp_free_domain(ctx, b)
