@@ -47,9 +47,11 @@ def lib():
         L.orc_gamma.argtypes = [dp]
         L.orc_domain_maps.argtypes = [i4, i4, i4, dp, dp, dp]
         L.orc_apply_hop.argtypes = [i4, ctypes.c_int, dp, i4, i4, dp, dp, ctypes.c_int]
-        L.orc_apply_dirac.argtypes = [i4, ctypes.c_int, dp, i4, i4, ctypes.c_double, dp, dp, ctypes.c_int]
-        L.orc_solve.argtypes = [i4, ctypes.c_int, dp, i4, i4, ctypes.c_double, dp, dp, ctypes.c_int,
-                                ctypes.c_double, ctypes.c_int, dp, dp]
+        L.orc_apply_dirac.argtypes = [i4, ctypes.c_int, dp, i4, i4, ctypes.c_double, ctypes.c_double, dp, dp,
+                                      ctypes.c_int]
+        L.orc_solve.argtypes = [i4, ctypes.c_int, dp, i4, i4, ctypes.c_double, ctypes.c_double, dp, dp,
+                                ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp]
+        L.orc_clover_field.argtypes = [i4, dp, ctypes.c_double, dp]
         L.orc_series_term.argtypes = [i4, i4, i4, dp, i4, i4, dp, dp, ctypes.c_int]
         L.orc_contract_local_trace.argtypes = [i4, i4, i4, dp, i4, dp]
         L.orc_contract_pion.argtypes = [i4, i4, i4, dp, dp]
@@ -125,20 +127,32 @@ def hop_power(U, L, bc, origin, extent, kappa, p, psi):
     return v
 
 
-def apply_dirac(U, L, bc, origin, extent, kappa, psi):
-    """D_Gamma psi on the box; psi has shape (ncol, n, 4, 3) or (n, 4, 3)."""
+def clover_field(U, L, csw):
+    """The clover term c_sw (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu}(x) of every site,
+    shape (V, 12, 12), rows and columns 3 spin + colour."""
+    U = _c(U)
+    V = int(np.prod(L))
+    out = np.zeros((V, 12, 12), dtype=np.complex128)
+    if lib().orc_clover_field(_i4(L), _ptr(U), float(csw), _ptr(out)):
+        raise ValueError("bad lattice")
+    return out
+
+
+def apply_dirac(U, L, bc, origin, extent, kappa, psi, csw=0.0):
+    """D_Gamma psi on the box; psi has shape (ncol, n, 4, 3) or (n, 4, 3).  csw != 0
+    adds the clover term (clover_field) at every site of the box."""
     U = _c(U)
     psi = _c(psi)
     out = np.zeros_like(psi)
     ncol = psi.shape[0] if psi.ndim == 4 else 1
-    rc = lib().orc_apply_dirac(_i4(L), bc, _ptr(U), _i4(origin), _i4(extent), float(kappa), _ptr(psi),
-                               _ptr(out), ncol)
+    rc = lib().orc_apply_dirac(_i4(L), bc, _ptr(U), _i4(origin), _i4(extent), float(kappa), float(csw),
+                               _ptr(psi), _ptr(out), ncol)
     if rc:
         raise ValueError("bad arguments")
     return out
 
 
-def solve(U, L, bc, origin, extent, kappa, eta, tol=1e-12, maxit=100000):
+def solve(U, L, bc, origin, extent, kappa, eta, tol=1e-12, maxit=100000, csw=0.0):
     """psi = D_Gamma^-1 eta per column; returns (psi, iters, relres, status)."""
     U = _c(U)
     eta = _c(eta)
@@ -146,8 +160,8 @@ def solve(U, L, bc, origin, extent, kappa, eta, tol=1e-12, maxit=100000):
     ncol = eta.shape[0]
     it = np.zeros(ncol, dtype=np.int32)
     rr = np.zeros(ncol, dtype=np.float64)
-    st = lib().orc_solve(_i4(L), bc, _ptr(U), _i4(origin), _i4(extent), float(kappa), _ptr(eta), _ptr(psi),
-                         ncol, float(tol), int(maxit), _ptr(it), _ptr(rr))
+    st = lib().orc_solve(_i4(L), bc, _ptr(U), _i4(origin), _i4(extent), float(kappa), float(csw), _ptr(eta),
+                         _ptr(psi), ncol, float(tol), int(maxit), _ptr(it), _ptr(rr))
     if st == 1:
         raise ValueError("bad arguments")
     return psi, it, rr, st
@@ -160,14 +174,14 @@ def local_index(L, origin, extent, x):
     return ((k[0] * extent[1] + k[1]) * extent[2] + k[2]) * extent[3] + k[3]
 
 
-def propagator(U, L, bc, origin, extent, kappa, src, tol=1e-12, maxit=100000):
+def propagator(U, L, bc, origin, extent, kappa, src, tol=1e-12, maxit=100000, csw=0.0):
     """12-column point-source propagator S(., x) on the box (columns 3*spin+colour)."""
     n = box_sites(extent)
     eta = np.zeros((12, n, 4, 3), dtype=np.complex128)
     l = local_index(L, origin, extent, src)
     for c in range(12):
         eta[c, l, c // 3, c % 3] = 1.0
-    return solve(U, L, bc, origin, extent, kappa, eta, tol, maxit)
+    return solve(U, L, bc, origin, extent, kappa, eta, tol, maxit, csw)
 
 
 def series_term(L, small_o, small_e, S_small, big_o, big_e, S_big):

@@ -264,10 +264,124 @@ int orc_apply_hop(const int L[4], int bc, const double *Ud, const int o[4], cons
     return 0;
 }
 
+/* ------------------------------------------------------ the clover term */
+
+/* 3x3 complex products for the clover leaves. */
+static void m3mul(const cplx a[9], const cplx b[9], cplx c[9]) {
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            cplx t = 0;
+            for (int k = 0; k < 3; k++) t += a[i * 3 + k] * b[k * 3 + j];
+            c[i * 3 + j] = t;
+        }
+}
+static void m3dag(const cplx a[9], cplx c[9]) {
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) c[i * 3 + j] = conj(a[j * 3 + i]);
+}
+static void m3copy(const cplx *a, cplx c[9]) { memcpy(c, a, 9 * sizeof(cplx)); }
+
+/* Global site index of x + s_mu mu + s_nu nu (periodic gauge field). */
+static int64_t shifted(const lat_t *lat, const int x[4], int mu, int smu, int nu, int snu) {
+    int y[4];
+    memcpy(y, x, sizeof(y));
+    y[mu] = (y[mu] + smu + lat->L[mu]) % lat->L[mu];
+    y[nu] = (y[nu] + snu + lat->L[nu]) % lat->L[nu];
+    return glob_index(lat, y);
+}
+
+/* Q_{mu nu}(x): the four plaquettes in the (mu, nu) plane that start and end at x,
+ * each traversed mu first (counterclockwise): the clover leaves. */
+static void clover_leaves(const lat_t *lat, const cplx *U, const int x[4], int mu, int nu, cplx Q[9]) {
+    cplx a[9], b[9], c[9], d[9], t1[9], t2[9], t3[9];
+    memset(Q, 0, 9 * sizeof(cplx));
+    /* x -> x+mu -> x+mu+nu -> x+nu -> x */
+    m3copy(link(lat, U, mu, shifted(lat, x, mu, 0, nu, 0)), a);
+    m3copy(link(lat, U, nu, shifted(lat, x, mu, 1, nu, 0)), b);
+    m3dag(link(lat, U, mu, shifted(lat, x, mu, 0, nu, 1)), c);
+    m3dag(link(lat, U, nu, shifted(lat, x, mu, 0, nu, 0)), d);
+    m3mul(a, b, t1), m3mul(t1, c, t2), m3mul(t2, d, t3);
+    for (int i = 0; i < 9; i++) Q[i] += t3[i];
+    /* x -> x+nu -> x+nu-mu -> x-mu -> x */
+    m3copy(link(lat, U, nu, shifted(lat, x, mu, 0, nu, 0)), a);
+    m3dag(link(lat, U, mu, shifted(lat, x, mu, -1, nu, 1)), b);
+    m3dag(link(lat, U, nu, shifted(lat, x, mu, -1, nu, 0)), c);
+    m3copy(link(lat, U, mu, shifted(lat, x, mu, -1, nu, 0)), d);
+    m3mul(a, b, t1), m3mul(t1, c, t2), m3mul(t2, d, t3);
+    for (int i = 0; i < 9; i++) Q[i] += t3[i];
+    /* x -> x-mu -> x-mu-nu -> x-nu -> x */
+    m3dag(link(lat, U, mu, shifted(lat, x, mu, -1, nu, 0)), a);
+    m3dag(link(lat, U, nu, shifted(lat, x, mu, -1, nu, -1)), b);
+    m3copy(link(lat, U, mu, shifted(lat, x, mu, -1, nu, -1)), c);
+    m3copy(link(lat, U, nu, shifted(lat, x, mu, 0, nu, -1)), d);
+    m3mul(a, b, t1), m3mul(t1, c, t2), m3mul(t2, d, t3);
+    for (int i = 0; i < 9; i++) Q[i] += t3[i];
+    /* x -> x-nu -> x-nu+mu -> x+mu -> x */
+    m3dag(link(lat, U, nu, shifted(lat, x, mu, 0, nu, -1)), a);
+    m3copy(link(lat, U, mu, shifted(lat, x, mu, 0, nu, -1)), b);
+    m3copy(link(lat, U, nu, shifted(lat, x, mu, 1, nu, -1)), c);
+    m3dag(link(lat, U, mu, shifted(lat, x, mu, 0, nu, 0)), d);
+    m3mul(a, b, t1), m3mul(t1, c, t2), m3mul(t2, d, t3);
+    for (int i = 0; i < 9; i++) Q[i] += t3[i];
+}
+
+/* The O(a)-improvement (clover) term of the Wilson-Dirac operator, site by site:
+ *   C(x) = c_sw (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu}(x),
+ *   sigma_{mu nu} = (i/2) [gamma_mu, gamma_nu],  F_{mu nu} = (Q_{mu nu} - Q_{nu mu}) / 8,
+ * the clover-leaf lattice field strength of the gauge field (periodic in every
+ * direction whatever the fermion boundary condition).  The paper names the
+ * improved operator (the footnotes of Sec. 4 and Sec. 5) without writing it down;
+ * this is the standard Sheikholeslami-Wohlert term.  out: [V][12][12] complex,
+ * rows and columns indexed 3 spin + colour. */
+static void clover_field(const lat_t *lat, const cplx g[5][4][4], const cplx *U, double csw, cplx *out) {
+    cplx sigma[4][4][4][4];
+    for (int mu = 0; mu < 4; mu++)
+        for (int nu = 0; nu < 4; nu++)
+            for (int s = 0; s < 4; s++)
+                for (int r = 0; r < 4; r++) {
+                    cplx t = 0;
+                    for (int q = 0; q < 4; q++) t += g[mu][s][q] * g[nu][q][r] - g[nu][s][q] * g[mu][q][r];
+                    sigma[mu][nu][s][r] = 0.5 * I * t;
+                }
+#pragma omp parallel for schedule(static)
+    for (int64_t site = 0; site < lat->V; site++) {
+        int x[4];
+        int64_t r = site;
+        for (int m = 3; m >= 0; m--) {
+            x[m] = (int)(r % lat->L[m]);
+            r /= lat->L[m];
+        }
+        cplx *C = out + site * 144;
+        memset(C, 0, 144 * sizeof(cplx));
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = 0; nu < 4; nu++) {
+                if (mu == nu) continue;
+                cplx Qa[9], Qb[9], F[9];
+                clover_leaves(lat, U, x, mu, nu, Qa);
+                clover_leaves(lat, U, x, nu, mu, Qb);
+                for (int i = 0; i < 9; i++) F[i] = (Qa[i] - Qb[i]) / 8.0;
+                for (int s = 0; s < 4; s++)
+                    for (int a = 0; a < 3; a++)
+                        for (int q = 0; q < 4; q++)
+                            for (int b = 0; b < 3; b++)
+                                C[(s * 3 + a) * 12 + q * 3 + b] += csw * 0.25 * I * sigma[mu][nu][s][q] * F[a * 3 + b];
+            }
+    }
+}
+
+int orc_clover_field(const int L[4], const double *Ud, double csw, double *outd) {
+    lat_t lat;
+    if (set_lat(&lat, L, 1)) return 1;
+    cplx g[5][4][4];
+    make_gamma(g);
+    clover_field(&lat, g, (const cplx *)Ud, csw, (cplx *)outd);
+    return 0;
+}
+
 /* D_Gamma of Sec. 2 applied to the box: D = D_w + m0 (App. A) written as
  *   (D psi)(y) = (4 + m0) psi(y) - 1/2 (Hop psi)(y),   4 + m0 = 1/(2 kappa),
  * with every term that involves a site outside the box set to zero. */
-static void apply_D(const lat_t *lat, const box_t *b, const cplx g[5][4][4], const cplx *U,
+static void apply_D(const lat_t *lat, const box_t *b, const cplx g[5][4][4], const cplx *U, const cplx *clov,
                     double kappa, const cplx *in, cplx *out) {
     double diag = 1.0 / (2.0 * kappa);
 #pragma omp parallel for schedule(static)
@@ -276,19 +390,39 @@ static void apply_D(const lat_t *lat, const box_t *b, const cplx g[5][4][4], con
         hop_site(lat, b, g, U, in, l, acc);
         for (int s = 0; s < 4; s++)
             for (int a = 0; a < 3; a++) out[l * 12 + s * 3 + a] = diag * in[l * 12 + s * 3 + a] - 0.5 * acc[s][a];
+        if (clov) {
+            /* the clover term is site-local: D[Gamma, Gamma] keeps it at every site of the box */
+            int k[4], x[4];
+            loc_coords(b, l, k);
+            glob_coords(lat, b, k, x);
+            const cplx *C = clov + glob_index(lat, x) * 144;
+            for (int i = 0; i < 12; i++) {
+                cplx t = 0;
+                for (int j = 0; j < 12; j++) t += C[i * 12 + j] * in[l * 12 + j];
+                out[l * 12 + i] += t;
+            }
+        }
     }
 }
 
+/* csw != 0 adds the clover term (clover_field). */
 int orc_apply_dirac(const int L[4], int bc, const double *Ud, const int o[4], const int e[4], double kappa,
-                    const double *ind, double *outd, int ncol) {
+                    double csw, const double *ind, double *outd, int ncol) {
     lat_t lat;
     box_t b;
     if (set_lat(&lat, L, bc) || set_box(&b, &lat, o, e) || !(kappa > 0)) return 1;
     cplx g[5][4][4];
     make_gamma(g);
+    cplx *clov = NULL;
+    if (csw != 0.0) {
+        clov = (cplx *)malloc((size_t)lat.V * 144 * sizeof(cplx));
+        if (!clov) return 1;
+        clover_field(&lat, g, (const cplx *)Ud, csw, clov);
+    }
     for (int c = 0; c < ncol; c++)
-        apply_D(&lat, &b, g, (const cplx *)Ud, kappa, (const cplx *)ind + (int64_t)c * b.n * 12,
+        apply_D(&lat, &b, g, (const cplx *)Ud, clov, kappa, (const cplx *)ind + (int64_t)c * b.n * 12,
                 (cplx *)outd + (int64_t)c * b.n * 12);
+    free(clov);
     return 0;
 }
 
@@ -328,8 +462,8 @@ static double norm2(const cplx *a, int64_t n) { return creal(dot(a, a, n)); }
  * recomputed true residual |eta - D psi| / |eta| <= tol; the recursion is
  * restarted from the true residual whenever the recursive residual reaches
  * tol without the true one doing so. */
-static int bicgstab(const lat_t *lat, const box_t *b, const cplx g[5][4][4], const cplx *U, double kappa,
-                    const cplx *eta, cplx *x, double tol, int maxit, int *iters, double *relres) {
+static int bicgstab(const lat_t *lat, const box_t *b, const cplx g[5][4][4], const cplx *U, const cplx *clov,
+                    double kappa, const cplx *eta, cplx *x, double tol, int maxit, int *iters, double *relres) {
     int64_t N = b->n * 12;
     cplx *r = calloc(N, sizeof(cplx)), *rh = calloc(N, sizeof(cplx)), *p = calloc(N, sizeof(cplx));
     cplx *v = calloc(N, sizeof(cplx)), *s = calloc(N, sizeof(cplx)), *t = calloc(N, sizeof(cplx));
@@ -344,7 +478,7 @@ static int bicgstab(const lat_t *lat, const box_t *b, const cplx g[5][4][4], con
     }
     for (int restart = 0; restart < 50 && it < maxit; restart++) {
         /* r = eta - D x */
-        apply_D(lat, b, g, U, kappa, x, r);
+        apply_D(lat, b, g, U, clov, kappa, x, r);
         for (int64_t i = 0; i < N; i++) r[i] = eta[i] - r[i];
         double rn = sqrt(norm2(r, N));
         if (rn <= tol * bn) {
@@ -361,12 +495,12 @@ static int bicgstab(const lat_t *lat, const box_t *b, const cplx g[5][4][4], con
             if (cabs(rho1) == 0.0) break;
             cplx beta = (rho1 / rho) * (alpha / omega);
             for (int64_t i = 0; i < N; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
-            apply_D(lat, b, g, U, kappa, p, v);
+            apply_D(lat, b, g, U, clov, kappa, p, v);
             cplx rv = dot(rh, v, N);
             if (cabs(rv) == 0.0) break;
             alpha = rho1 / rv;
             for (int64_t i = 0; i < N; i++) s[i] = r[i] - alpha * v[i];
-            apply_D(lat, b, g, U, kappa, s, t);
+            apply_D(lat, b, g, U, clov, kappa, s, t);
             double tt = norm2(t, N);
             omega = (tt > 0) ? dot(t, s, N) / tt : 0.0;
             for (int64_t i = 0; i < N; i++) {
@@ -378,7 +512,7 @@ static int bicgstab(const lat_t *lat, const box_t *b, const cplx g[5][4][4], con
         }
     }
     /* final true residual */
-    apply_D(lat, b, g, U, kappa, x, r);
+    apply_D(lat, b, g, U, clov, kappa, x, r);
     for (int64_t i = 0; i < N; i++) r[i] = eta[i] - r[i];
     *relres = (bn > 0) ? sqrt(norm2(r, N)) / bn : 0.0;
     *iters = it;
@@ -395,19 +529,26 @@ done:
 
 /* Solve D_Gamma psi_c = eta_c for ncol columns (Sec. 2, Eq. diric).  Returns 0
  * when every column reached tol, 2 if some did not, 1 on bad arguments. */
-int orc_solve(const int L[4], int bc, const double *Ud, const int o[4], const int e[4], double kappa,
+int orc_solve(const int L[4], int bc, const double *Ud, const int o[4], const int e[4], double kappa, double csw,
               const double *etad, double *psid, int ncol, double tol, int maxit, int *iters, double *relres) {
     lat_t lat;
     box_t b;
     if (set_lat(&lat, L, bc) || set_box(&b, &lat, o, e) || !(kappa > 0)) return 1;
     cplx g[5][4][4];
     make_gamma(g);
+    cplx *clov = NULL;
+    if (csw != 0.0) {
+        clov = (cplx *)malloc((size_t)lat.V * 144 * sizeof(cplx));
+        if (!clov) return 1;
+        clover_field(&lat, g, (const cplx *)Ud, csw, clov);
+    }
     int worst = 0;
     for (int c = 0; c < ncol; c++) {
-        int st = bicgstab(&lat, &b, g, (const cplx *)Ud, kappa, (const cplx *)etad + (int64_t)c * b.n * 12,
+        int st = bicgstab(&lat, &b, g, (const cplx *)Ud, clov, kappa, (const cplx *)etad + (int64_t)c * b.n * 12,
                           (cplx *)psid + (int64_t)c * b.n * 12, tol, maxit, &iters[c], &relres[c]);
         if (st > worst) worst = st;
     }
+    free(clov);
     return worst;
 }
 

@@ -566,3 +566,149 @@ def test_free_field_correlators_match_golden_values():
     assert _rel(oracle.pion(L, (0, 0, 0, 0), L, S), np.array(g["pion"])) < 1e-11
     want = np.array(g["nucleon_re"]) + 1j * np.array(g["nucleon_im"])
     assert _rel(oracle.nucleon(L, (0, 0, 0, 0), L, S), want) < 1e-10
+
+
+# ------------------------------------------------------------ clover (O(a)-improvement) term
+#
+# The paper names the O(a)-improved operator (footnotes of Sec. 4 and Sec. 5)
+# without writing it; the oracle uses the Sheikholeslami-Wohlert term
+# c_sw (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu}(x) with the clover-leaf F.
+# These tests pin it with constant abelian fields, whose field strength and
+# clover spectrum are known in closed form, and with the symmetries of D.
+
+def _constant_flux(L, planes):
+    """SU(3) links that are diagonal phases giving every plaquette of the (mu, nu)
+    plane the phase exp(i n B q_c) per colour c (q = charges, sum q = 0) and every
+    other plaquette 1: U_nu(x) = exp(i B x_mu q), U_mu(x) = exp(-i B L_mu x_nu q) on
+    the last slice x_mu = L_mu - 1, with B = 2 pi n / (L_mu L_nu).
+    planes: list of (mu, nu, n, q)."""
+    V = int(np.prod(L))
+    x = np.stack(np.unravel_index(np.arange(V), L), axis=1)
+    ph = np.zeros((4, V, 3))
+    for mu, nu, n, q in planes:
+        B = 2 * np.pi * n / (L[mu] * L[nu])
+        q = np.asarray(q, dtype=float)
+        ph[nu] += np.outer(B * x[:, mu], q)
+        last = x[:, mu] == L[mu] - 1
+        ph[mu][last] -= np.outer(B * L[mu] * x[last, nu], q)
+    U = np.zeros((4, V, 3, 3), dtype=np.complex128)
+    for c in range(3):
+        U[:, :, c, c] = np.exp(1j * ph[:, :, c])
+    return U
+
+
+@pytest.mark.parametrize("plane", [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)])
+def test_clover_term_constant_field_spectrum(plane):
+    """One constant field in the (mu, nu) plane: F_{mu nu} = i sin(B q_c) per colour, so
+    the clover term -(c_sw/2) sigma_{mu nu} (x) diag sin(B q) has the eigenvalues
+    +-(c_sw/2) sin(B q_c), each twice (sigma_{mu nu} has eigenvalues +-1, twice each),
+    at every site."""
+    L, csw = (4, 6, 4, 6), 1.7
+    q = (1.0, 2.0, -3.0)
+    mu, nu = plane
+    U = _constant_flux(L, [(mu, nu, 1, q)])
+    C = oracle.clover_field(U, L, csw)
+    B = 2 * np.pi / (L[mu] * L[nu])
+    want = np.sort(np.concatenate([[s * 0.5 * csw * np.sin(B * qc)] * 2 for qc in q for s in (1, -1)]))
+    for site in (0, 17, 300, int(np.prod(L)) - 1):
+        got = np.sort(np.linalg.eigvalsh(C[site]))
+        assert np.allclose(got, want, atol=1e-13), (site, got, want)
+
+
+def test_clover_term_two_planes_relative_orientation():
+    """Fields in the (0,1) and (2,3) planes together: sigma_01 sigma_23 = -gamma_5 fixes
+    how the two terms combine; per colour the spectrum is +-(c_sw/2)(a - b) and
+    +-(c_sw/2)(a + b) with a, b the two sin(B q) (a dropped 1/2, a wrong sigma or a
+    wrong plane orientation changes it)."""
+    L, csw = (6, 4, 4, 6), 0.9
+    qa, qb = (1.0, -2.0, 1.0), (2.0, 1.0, -3.0)
+    U = _constant_flux(L, [(0, 1, 1, qa), (2, 3, 1, qb)])
+    C = oracle.clover_field(U, L, csw)
+    Ba, Bb = 2 * np.pi / (L[0] * L[1]), 2 * np.pi / (L[2] * L[3])
+    want = []
+    for c in range(3):
+        a, b = np.sin(Ba * qa[c]), np.sin(Bb * qb[c])
+        want += [0.5 * csw * v for v in (a - b, b - a, a + b, -a - b)]
+    want = np.sort(want)
+    for site in (0, 55, 250):
+        assert np.allclose(np.sort(np.linalg.eigvalsh(C[site])), want, atol=1e-13)
+
+
+def test_clover_term_vanishes_for_unit_links_and_is_hermitian(field44):
+    L, U = field44
+    assert np.abs(oracle.clover_field(synth.unit_gauge_field(L), L, 1.5)).max() < 1e-15
+    C = oracle.clover_field(U, L, 1.5)
+    assert np.abs(C - np.conj(np.swapaxes(C, 1, 2))).max() < 1e-14
+    # commutes with gamma_5 (sigma_{mu nu} does): block diagonal in the chiral spin pairs
+    g5 = np.kron(oracle.gamma()[4], np.eye(3))
+    assert np.abs(C @ g5 - g5 @ C).max() < 1e-14
+
+
+def test_clover_operator_adds_the_site_term(field44):
+    """D(c_sw) - D(0) is site-local on a Dirichlet box and equals the clover term of the
+    sites of the box (links outside the box included: D_Gamma = D[Gamma, Gamma])."""
+    L, U = field44
+    o, e = (3, 1, 0, 2), (2, 3, 4, 2)
+    gi, _, _ = oracle.domain_maps(L, o, e)
+    psi = synth.random_spinor(2, gi.size, 5)
+    d = oracle.apply_dirac(U, L, AP, o, e, 0.13, psi, csw=1.3) - oracle.apply_dirac(U, L, AP, o, e, 0.13, psi)
+    C = oracle.clover_field(U, L, 1.3)
+    want = np.einsum("nij,cnj->cni", C[gi], psi.reshape(2, gi.size, 12)).reshape(psi.shape)
+    assert _rel(d, want) < 1e-13
+
+
+def test_clover_gamma5_hermiticity(field44):
+    L, U = field44
+    o, e = (3, 1, 0, 2), (2, 3, 4, 2)
+    n = int(np.prod(e))
+    g5 = oracle.gamma()[4]
+    phi = synth.random_spinor(1, n, 1)
+    psi = synth.random_spinor(1, n, 2)
+    g5psi = np.einsum("ab,cnbk->cnak", g5, psi)
+    lhs = np.vdot(phi, np.einsum("ab,cnbk->cnak", g5, oracle.apply_dirac(U, L, AP, o, e, 0.13, g5psi, csw=1.4)))
+    rhs = np.vdot(oracle.apply_dirac(U, L, AP, o, e, 0.13, phi, csw=1.4), psi)
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+
+
+def test_clover_gauge_covariance(field44):
+    """With the clover term the propagator still transforms as S' = Lam(y) S Lam(x)^+:
+    a leaf with its links in the wrong order would break it."""
+    L, U = field44
+    V = 256
+    Lam = synth.random_gauge_transform(V, 78)
+    Lr = Lam.reshape(L + (3, 3))
+    Up = np.empty_like(U)
+    for mu in range(4):
+        Ur = U[mu].reshape(L + (3, 3))
+        Lp = np.roll(Lr, -1, axis=mu)
+        Up[mu] = (Lr @ Ur @ np.conj(np.swapaxes(Lp, -1, -2))).reshape(V, 3, 3)
+    C, Cp = oracle.clover_field(U, L, 1.2), oracle.clover_field(Up, L, 1.2)
+    Lam12 = np.einsum("st,nab->nsatb", np.eye(4), Lam).reshape(V, 12, 12)
+    assert np.abs(Cp - Lam12 @ C @ np.conj(np.swapaxes(Lam12, 1, 2))).max() < 1e-13
+    o, e, src = (3, 0, 1, 0), (3, 4, 2, 4), (3, 1, 1, 2)
+    S, *_ = oracle.propagator(U, L, AP, o, e, 0.13, src, csw=1.2)
+    Sp, *_ = oracle.propagator(Up, L, AP, o, e, 0.13, src, csw=1.2)
+    assert _rel(oracle.pion(L, o, e, Sp), oracle.pion(L, o, e, S)) < 1e-10
+    assert _rel(oracle.nucleon(L, o, e, Sp), oracle.nucleon(L, o, e, S)) < 1e-9
+
+
+def test_clover_domain_propagator_is_inverse_of_sub_block(field44):
+    """S^(i) with the clover term = inverse of the (Gamma, Gamma) block of the dense
+    improved operator assembled column by column."""
+    L, U = field44
+    o, e = (1, 1, 0, 0), (2, 2, 4, 2)
+    n = int(np.prod(e))
+    csw, kappa = 1.1, 0.12
+    Dm = np.zeros((12 * n, 12 * n), dtype=np.complex128)
+    unit = np.zeros((1, n, 4, 3), dtype=np.complex128)
+    for j in range(12 * n):
+        unit.reshape(-1)[:] = 0
+        unit.reshape(-1)[j] = 1.0
+        Dm[:, j] = oracle.apply_dirac(U, L, AP, o, e, kappa, unit, csw=csw).reshape(-1)
+    src = (2, 1, 3, 1)
+    S, _, rr, st = oracle.propagator(U, L, AP, o, e, kappa, src, csw=csw)
+    assert st == 0
+    Sinv = np.linalg.inv(Dm)
+    l = oracle.local_index(L, o, e, src)
+    for c in range(12):
+        assert _rel(S[c].reshape(-1), Sinv[:, 12 * l + c]) < 1e-10
