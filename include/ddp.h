@@ -54,7 +54,7 @@ extern "C" {
 typedef enum {
     DDP_OK = 0,
     DDP_ERR_INVALID_ARG = 1,   /* bad size, box, source, kappa, id or non-SU(3)/non-finite links */
-    DDP_ERR_UNSUPPORTED = 2,   /* csw != 0, odd lattice extent, odd e_3 */
+    DDP_ERR_UNSUPPORTED = 2,   /* odd lattice extent, odd e_3, csw != 0 when serving */
     DDP_ERR_OOM = 3,           /* device allocation failed or over the context's memory budget */
     DDP_ERR_NOT_CONVERGED = 4, /* a solve missed its tolerance within the iteration caps */
     DDP_ERR_CUDA = 5,          /* a CUDA runtime error (message in ddp_last_error) */
@@ -138,8 +138,12 @@ int ddp_domain_sites(ddp_ctx *ctx, int domain_id, int64_t *n_sites, int64_t *glo
 
 /* out = D_Gamma psi for ncol columns (App. A, Sec. 2).  precision FP64 uses
  * the FP64 links; the MIXED_* values apply the low-precision stencil of the
- * inner solver (FP32 arithmetic on the stored copies). */
-int ddp_apply_dirac(ddp_ctx *ctx, int domain_id, double kappa, const double *psi, double *out, int ncol,
+ * inner solver (FP32 arithmetic on the stored copies).  csw != 0 adds the
+ * O(a)-improvement (clover) term c_sw (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu}(x)
+ * with the clover-leaf field strength F = (Q_{mu nu} - Q_{nu mu}) / 8 of the whole
+ * gauge field (the improved operator the footnotes of Sec. 4 and Sec. 5 refer to);
+ * the term is site-local, so D_Gamma keeps it at every site of the domain. */
+int ddp_apply_dirac(ddp_ctx *ctx, int domain_id, double kappa, double csw, const double *psi, double *out, int ncol,
                     int precision);
 
 /* out = (kappa D_hop)^p psi on the domain, in FP64: p applications of the
@@ -160,7 +164,13 @@ int ddp_hop_power(ddp_ctx *ctx, int domain_id, double kappa, int p, const double
 /* Domain propagator S^(i)(y,x) = D_Gamma^{-1}(y,x) (Eq. diric) for the 12
  * spin-colour point sources at global site src (which must lie in the
  * domain).  Stops when every column has |eta - D_Gamma psi|_2 / |eta|_2 <= tol
- * (FP64, unpreconditioned operator).  csw must be 0 (no clover term).
+ * (FP64, unpreconditioned operator).  csw != 0 solves with the clover term
+ * (see ddp_apply_dirac): the even-odd inner operator becomes
+ * 1 - kappa^2 T_ee^-1 H_eo T_oo^-1 H_oe with T = 1 + 2 kappa C the site-local
+ * part of 2 kappa D; T and T^-1 are built once per (gauge field, kappa, c_sw) and
+ * kept with the gauge field (the 4 most recently used pairs; one call may use at
+ * most 4 distinct pairs, else DDP_ERR_UNSUPPORTED).  DDP_ERR_INVALID_ARG if T is
+ * singular at some site.
  * S_out: [12][n_sites][4][3].  On DDP_ERR_NOT_CONVERGED S_out holds the best
  * iterate and info the residuals.  info may be NULL. */
 int ddp_solve_propagator(ddp_ctx *ctx, int domain_id, double kappa, double csw, const int src[4], double tol,
@@ -174,7 +184,7 @@ int ddp_solve_sources(ddp_ctx *ctx, int domain_id, double kappa, double csw, con
 typedef struct {
     int domain_id;
     double kappa;
-    double csw;          /* must be 0 */
+    double csw;          /* clover coefficient c_sw (0: plain Wilson; see ddp_apply_dirac) */
     int src[4];          /* point source (used when eta == NULL) */
     const double *eta;   /* NULL: 12 point-source columns at src; else ncol sources */
     int ncol;            /* 12 for point sources */
@@ -229,7 +239,7 @@ int ddp_boundary_source(ddp_ctx *ctx, int domain_from, const double *psi, int do
  *    nothing the call computed is uploaded again.  Device-resident copies live
  *    in the context until its next call of this function.
  *  - Returns DDP_ERR_NOT_CONVERGED (with every output written) when a solve missed
- *    tol; infos: n entries or NULL.  csw != 0: DDP_ERR_UNSUPPORTED. */
+ *    tol; infos: n entries or NULL.  csw: as in ddp_solve_propagator. */
 int ddp_propagator_series(ddp_ctx *ctx, int n, const int *domain_ids, double kappa, double csw, const int src[4],
                           double tol, int precision, double *const *S_out, double *const *T_out, int contract_mask,
                           double *C_out, ddp_solve_info *infos);

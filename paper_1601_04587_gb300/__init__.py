@@ -75,7 +75,7 @@ def lib():
             "ddp_set_domain": ([vp, i, i4, i4, i4], i),
             "ddp_free_domain": ([vp, i], i),
             "ddp_domain_sites": ([vp, i, ctypes.POINTER(ctypes.c_int64), vp, vp], i),
-            "ddp_apply_dirac": ([vp, i, d, vp, vp, i, i], i),
+            "ddp_apply_dirac": ([vp, i, d, d, vp, vp, i, i], i),
             "ddp_hop_power": ([vp, i, d, i, vp, vp, i], i),
             "ddp_boundary_source": ([vp, i, vp, i, vp, i], i),
             "ddp_solve_propagator": ([vp, i, d, d, i4, d, i, vp, ctypes.POINTER(ddp_solve_info)], i),
@@ -194,9 +194,9 @@ def ddp_domain_sites(ctx, domain_id, global_index_out=None, eo_index_out=None) -
     return n.value
 
 
-def ddp_apply_dirac(ctx, domain_id, kappa, psi, out, ncol, precision=DDP_PREC_FP64):
-    return _check(ctx, lib().ddp_apply_dirac(ctx, int(domain_id), float(kappa), _ptr(psi), _ptr(out), int(ncol),
-                                             int(precision)), "ddp_apply_dirac")
+def ddp_apply_dirac(ctx, domain_id, kappa, psi, out, ncol, precision=DDP_PREC_FP64, csw=0.0):
+    return _check(ctx, lib().ddp_apply_dirac(ctx, int(domain_id), float(kappa), float(csw), _ptr(psi), _ptr(out),
+                                             int(ncol), int(precision)), "ddp_apply_dirac")
 
 
 def ddp_hop_power(ctx, domain_id, kappa, p, psi, out, ncol=12):

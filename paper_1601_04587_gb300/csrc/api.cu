@@ -84,6 +84,11 @@ void make_plan(const std::vector<Job> &jobs, int prec, const EngineParams &prm, 
         it.links = j.g->links(prec);
         it.links64 = j.g->u64;
         it.gV = j.g->V;
+        if (j.clov) {
+            it.clov = (prec == DDP_PREC_FP64) ? (const void *)j.clov->t64 : (const void *)j.clov->t32;
+            it.clovinv = (prec == DDP_PREC_FP64) ? (const void *)j.clov->ti64 : (const void *)j.clov->ti32;
+            it.clov64 = j.clov->t64;
+        }
         blk += it.ntiles * it.ncg;
         solve += j.ncol;
         fbase += (int64_t)j.ncol * it.nh;
@@ -738,9 +743,9 @@ int ddp_domain_sites(ddp_ctx *ctx, int domain_id, int64_t *n_sites, int64_t *gid
     return DDP_OK;
 }
 
-int ddp_apply_dirac(ddp_ctx *ctx, int domain_id, double kappa, const double *psi, double *out, int ncol,
+int ddp_apply_dirac(ddp_ctx *ctx, int domain_id, double kappa, double csw, const double *psi, double *out, int ncol,
                     int precision) {
-    if (!ctx || !psi || !out || ncol < 1 || !(kappa > 0)) return DDP_ERR_INVALID_ARG;
+    if (!ctx || !psi || !out || ncol < 1 || !(kappa > 0) || !std::isfinite(csw)) return DDP_ERR_INVALID_ARG;
     if (precision < 0 || precision > 3) return DDP_ERR_INVALID_ARG;
     const DomainDev *d;
     const GaugeDev *g;
@@ -759,6 +764,7 @@ int ddp_apply_dirac(ddp_ctx *ctx, int domain_id, double kappa, const double *psi
     memcpy(j.e, d->e, sizeof(j.e));
     j.kappa = kappa;
     j.ncol = ncol;
+    if (csw != 0.0 && (rc = clover_for(ctx, *const_cast<GaugeDev *>(g), kappa, csw, &j.clov))) return rc;
     switch (precision) {
         case DDP_PREC_FP64: rc = apply_dirac_impl<PF64>(ctx, j, (const double *)si.dev, (double *)so.dev, precision); break;
         case DDP_PREC_MIXED_FP32: rc = apply_dirac_impl<PF32>(ctx, j, (const double *)si.dev, (double *)so.dev, precision); break;
@@ -833,10 +839,10 @@ static int run_solves(ddp_ctx *ctx, const ddp_solve_req *reqs, int n, int precis
     auto t0 = std::chrono::steady_clock::now();
     std::vector<Job> jobs(n);
     std::vector<std::unique_ptr<Staged>> st_in(n), st_out(n);
+    int clover_pairs = 0;
     for (int i = 0; i < n; i++) {
         const ddp_solve_req &r = reqs[i];
-        if (r.csw != 0.0) return DDP_ERR_UNSUPPORTED;
-        if (!(r.kappa > 0) || !(r.tol > 0) || !r.out) return DDP_ERR_INVALID_ARG;
+        if (!(r.kappa > 0) || !(r.tol > 0) || !r.out || !std::isfinite(r.csw)) return DDP_ERR_INVALID_ARG;
         const DomainDev *d;
         const GaugeDev *g;
         int rc = find_domain(ctx, r.domain_id, &d, &g);
@@ -844,6 +850,15 @@ static int run_solves(ddp_ctx *ctx, const ddp_solve_req *reqs, int n, int precis
         Job &j = jobs[i];
         memset(&j, 0, sizeof(j));
         j.g = g;
+        if (r.csw != 0.0) {
+            // clover term of (gauge, kappa, c_sw): at most CLOVER_CACHE distinct pairs per call
+            bool seen = false;
+            for (int k = 0; k < i; k++)
+                seen = seen || (reqs[k].csw != 0.0 && jobs[k].g == g && reqs[k].kappa == r.kappa &&
+                                reqs[k].csw == r.csw);
+            if (!seen && ++clover_pairs > CLOVER_CACHE) return DDP_ERR_UNSUPPORTED;
+            if ((rc = clover_for(ctx, *const_cast<GaugeDev *>(g), r.kappa, r.csw, &j.clov))) return rc;
+        }
         memcpy(j.o, d->o, sizeof(j.o));
         memcpy(j.e, d->e, sizeof(j.e));
         j.kappa = r.kappa;
@@ -983,7 +998,6 @@ int ddp_propagator_series(ddp_ctx *ctx, int n, const int *domain_ids, double kap
     const int allowed = (1 << DDP_CONTRACT_PSEUDO_LOCAL) | (1 << DDP_CONTRACT_NUCLEON) | (1 << DDP_CONTRACT_PION);
     if (contract_mask & ~allowed) return DDP_ERR_INVALID_ARG;
     if (contract_mask && !C_out) return DDP_ERR_INVALID_ARG;
-    if (csw != 0.0) return DDP_ERR_UNSUPPORTED;
     std::vector<const DomainDev *> dom(n);
     std::vector<const GaugeDev *> gau(n);
     for (int i = 0; i < n; i++) {

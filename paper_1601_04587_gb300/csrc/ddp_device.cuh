@@ -351,6 +351,11 @@ struct Item {
     const void *links;    // links of the launch's storage precision
     const void *links64;  // FP64 links
     int64_t gV;           // lattice volume (link field row length)
+    // clover term (clover.cuh), NULL without it: T and T^-1 in the launch's arithmetic
+    // (FP64 packed for the FP64 path, FP32 packed otherwise) and T in FP64
+    const void *clov;
+    const void *clovinv;
+    const void *clov64;
 };
 
 struct Launch {

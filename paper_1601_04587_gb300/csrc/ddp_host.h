@@ -12,8 +12,17 @@
 
 #include "ddp.h"
 #include "ddp_kernels.cuh"
+#include "clover.cuh"
 
 namespace ddp {
+
+// Clover fields T = 1 + 2 kappa C and T^-1 of one (gauge, kappa, c_sw) (clover.cuh).
+struct CloverDev {
+    double kappa = 0, csw = 0;
+    double2 *t64 = nullptr, *ti64 = nullptr;  // [36][V]
+    float4 *t32 = nullptr, *ti32 = nullptr;   // [18][V]
+    ~CloverDev();
+};
 
 // Resident gauge field: FP64 full links and 2-row low-precision copies, all
 // in the global even-odd order [mu][chunk][V].
@@ -25,6 +34,7 @@ struct GaugeDev {
     float4 *u32 = nullptr;   // [4][3][V]
     uint2 *u16 = nullptr;    // [4][3][V]
     uint2 *ub16 = nullptr;   // [4][3][V]
+    std::vector<std::unique_ptr<CloverDev>> clov;  // clover fields built for this field
     const void *links(int prec) const {
         switch (prec) {
             case DDP_PREC_FP64: return u64;
@@ -51,6 +61,7 @@ struct Job {
     const double *eta;  // device, user layout; nullptr: 12 point sources at src_l
     int src_l;
     double *out;        // device, user layout
+    const CloverDev *clov;  // clover term of (g, kappa, c_sw), or nullptr (c_sw = 0)
 };
 
 struct JobInfo {
@@ -131,6 +142,11 @@ struct StreamJoin {
 };
 
 int set_cuda_error(ddp_ctx *ctx, cudaError_t e, const char *where);
+
+// The clover fields of (g, kappa, c_sw), built on first use and cached with g
+// (least recently used first out, CLOVER_CACHE pairs).
+constexpr int CLOVER_CACHE = 4;
+int clover_for(ddp_ctx *ctx, GaugeDev &g, double kappa, double csw, const CloverDev **out);
 
 #define DDP_CUDA(ctx, call)                                          \
     do {                                                            \

@@ -6,6 +6,7 @@
 #include <type_traits>
 
 #include "ddp_device.cuh"
+#include "clover.cuh"
 
 namespace ddp {
 
@@ -45,7 +46,13 @@ struct Partials {
     double *n;
 };
 
-enum Epi { EPI_PLAIN = 0, EPI_MHAT = 1, EPI_AXPY_K = 2, EPI_DIRAC = 3, EPI_RESID = 4 };
+// Epilogues of the hopping kernel (acc = the hopping sum, v1, v2 operands at the
+// output site; T / T^-1 the clover matrices of the output site, identity without
+// the clover term):
+//   PLAIN  T^-1 acc                 MHAT  v1 - kappa^2 T^-1 acc
+//   AXPY_K v1 + kappa T^-1 acc      RHS   T^-1 (v1 + kappa acc)
+//   DIRAC  T v1 / (2 kappa) - acc/2 RESID v2 - T v1 / (2 kappa) + acc/2
+enum Epi { EPI_PLAIN = 0, EPI_MHAT = 1, EPI_AXPY_K = 2, EPI_DIRAC = 3, EPI_RESID = 4, EPI_RHS = 5 };
 enum Dot { DOT_NONE = 0, DOT_RHAT = 1, DOT_TS = 2, DOT_NORM = 3 };
 
 struct HopArgs {
@@ -143,47 +150,52 @@ __device__ __forceinline__ void load_item(const Launch &L, Item &dst) {
 // memory once and shared by the CG column-threads of every site.
 // Epilogue of the hopping kernels: out = combination of acc and same-parity
 // operands, stored in the storage format, plus the requested dot products.
-template <class P, int EPI, int DOT>
+template <class P, int EPI, int DOT, bool CLOV>
 __device__ __forceinline__ void hop_store_epilogue(const HopArgs &a, const Item &it, const TileCoord &tc,
                                                    const cx<typename P::real> acc[4][3], typename P::real &cre,
                                                    typename P::real &cim, typename P::real &nn) {
     using R = typename P::real;
-        R o[24];
+    R o[24];
     int64_t i = tc.cb + tc.h;
     const R kap = (R)it.kappa;
+    // clover matrices of the output site (T^-1 on the hopping sum, T on v1)
+    const bool clov = CLOV && it.clovinv;
+    int64_t row = 0;
+    if (clov) row = site_row(it, tc.h, a.p);
+    R h[24];
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            h[2 * (3 * s + c)] = acc[s][c].re;
+            h[2 * (3 * s + c) + 1] = acc[s][c].im;
+        }
+    if (clov && (EPI == EPI_PLAIN || EPI == EPI_MHAT || EPI == EPI_AXPY_K)) clover_apply<R>(it.clovinv, it.gV, row, h);
     if (EPI == EPI_PLAIN) {
 #pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                o[2 * (3 * s + c)] = acc[s][c].re;
-                o[2 * (3 * s + c) + 1] = acc[s][c].im;
-            }
+        for (int j = 0; j < 24; j++) o[j] = h[j];
     } else {
         R w[24];
         load_spinor<P>(a.v1, i, w);
+        if (clov && (EPI == EPI_DIRAC || EPI == EPI_RESID))
+            clover_apply<R>(EPI == EPI_RESID ? it.clov64 : it.clov, it.gV, row, w);
         R cw, ca;
         if (EPI == EPI_MHAT) {
             cw = R(1);
             ca = -kap * kap;
-        } else if (EPI == EPI_AXPY_K) {
+        } else if (EPI == EPI_AXPY_K || EPI == EPI_RHS) {
             cw = R(1);
             ca = kap;
         } else if (EPI == EPI_DIRAC) {
             cw = R(1) / (R(2) * kap);
             ca = R(-0.5);
-        } else {  // EPI_RESID: eta - x/(2 kappa) + acc/2
+        } else {  // EPI_RESID: eta - T x/(2 kappa) + acc/2
             cw = -R(1) / (R(2) * kap);
             ca = R(0.5);
         }
 #pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                int j = 2 * (3 * s + c);
-                o[j] = cw * w[j] + ca * acc[s][c].re;
-                o[j + 1] = cw * w[j + 1] + ca * acc[s][c].im;
-            }
+        for (int j = 0; j < 24; j++) o[j] = cw * w[j] + ca * h[j];
+        if (clov && EPI == EPI_RHS) clover_apply<R>(it.clovinv, it.gV, row, o);
         if (EPI == EPI_RESID) {
             load_spinor<P>(a.v2, i, w);
 #pragma unroll
@@ -216,7 +228,7 @@ __device__ __forceinline__ void hop_store_epilogue(const HopArgs &a, const Item 
         for (int j = 0; j < 24; j++) s += o[j] * o[j];
         nn = s;
     }
-    }
+}
 
 // A staged link in shared memory: 9 complex, one 8-byte (FP32 compute) or
 // 16-byte (FP64) access each.
@@ -239,7 +251,7 @@ __device__ __forceinline__ void get_link(const R *d, cx<R> u[3][3]) {
 }
 
 
-template <class P, int EPI, int DOT>
+template <class P, int EPI, int DOT, bool CLOV = false>
 __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_hop(HopArgs a) {
     using R = typename P::real;
     constexpr int TSMAX = HOP_TS;
@@ -308,7 +320,7 @@ __global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_
         DDP_HOP_STEP(6)
         DDP_HOP_STEP(7)
 #undef DDP_HOP_STEP
-        hop_store_epilogue<P, EPI, DOT>(a, it, tc, acc, cre, cim, nn);
+        hop_store_epilogue<P, EPI, DOT, CLOV>(a, it, tc, acc, cre, cim, nn);
     }
     if (DOT != DOT_NONE) block_partials(it, a.L, tc, cre, cim, nn, a.part, DOT == DOT_RHAT || DOT == DOT_TS,
                                         DOT == DOT_TS || DOT == DOT_NORM);
@@ -509,9 +521,12 @@ struct ConvArgs {
     FieldView lo;   // storage-format field
     FieldView hi;   // FP64 field
     const SolveState *st;
+    int p;          // parity of the sites
+    int clov;       // k_to_low: apply the clover T^-1 of the site (items that have one)
 };
 
-// lo = scale * hi  (scale = 2 kappa / sigma: the normalised defect of Sec. "mixed")
+// lo = scale * hi  (scale = 2 kappa / sigma: the normalised defect), times T^-1
+// of the site when a.clov is set
 template <class P>
 __global__ void __launch_bounds__(512) k_to_low(ConvArgs a) {
     using R = typename P::real;
@@ -526,6 +541,7 @@ __global__ void __launch_bounds__(512) k_to_low(ConvArgs a) {
     R w[24];
 #pragma unroll
     for (int j = 0; j < 24; j++) w[j] = (R)(sc * v[j]);
+    if (a.clov && it.clovinv) clover_apply<R>(it.clovinv, it.gV, site_row(it, tc.h, a.p), w);
     store_spinor<P>(a.lo, i, w);
 }
 

@@ -23,10 +23,10 @@
 
 namespace ddp {
 
-// One launch of the hopping term.
-template <class Q, int EPI, int DOT>
+// One launch of the hopping term (CL: with the clover term of the items that have one).
+template <class Q, int EPI, int DOT, bool CL = false>
 inline void launch_hop(ddp_ctx *ctx, int nblocks, int threads, const HopArgs &a) {
-    k_hop<Q, EPI, DOT><<<nblocks, threads, 0, ctx->stream>>>(a);
+    k_hop<Q, EPI, DOT, CL><<<nblocks, threads, 0, ctx->stream>>>(a);
 }
 
 template <class P>
@@ -46,6 +46,7 @@ struct Engine {
     cudaGraphExec_t loop_exec = nullptr;
     cudaGraph_t loop_graph = nullptr;
     long launches = 0;
+    bool clov = false;  // some item of the plan has a clover term
 
     ~Engine() {
         if (loop_exec) cudaGraphExecDestroy(loop_exec);
@@ -68,9 +69,9 @@ struct Engine {
         return a;
     }
 
-    template <class Q, int EPI, int DOT>
+    template <class Q, int EPI, int DOT, bool CL = false>
     void hop(const HopArgs &a) {
-        launch_hop<Q, EPI, DOT>(ctx, plan.nblocks, threads, a);
+        launch_hop<Q, EPI, DOT, CL>(ctx, plan.nblocks, threads, a);
         launches++;
     }
 
@@ -117,12 +118,15 @@ struct Engine {
         launches++;
     }
 
-    void conv(bool to_low, FieldView lo, FieldView hi) {
+    // to_low: lo = scale hi (times T^-1 of the site when clov_inv); else hi += sigma lo
+    void conv(bool to_low, FieldView lo, FieldView hi, int par = 0, bool clov_inv = false) {
         ConvArgs a;
         a.L = L;
         a.lo = lo;
         a.hi = hi;
         a.st = d_st;
+        a.p = par;
+        a.clov = clov_inv ? 1 : 0;
         if (to_low)
             k_to_low<P><<<plan.nblocks, threads, 0, ctx->stream>>>(a);
         else
@@ -130,19 +134,27 @@ struct Engine {
         launches++;
     }
 
-    // One BiCGStab iteration on the Schur complement (van der Vorst 1992).
-    void iteration_body() {
+    // One BiCGStab iteration on the Schur complement (van der Vorst 1992); with the
+    // clover term the operator is 1 - kappa^2 T_ee^-1 H_eo T_oo^-1 H_oe.
+    template <bool CL>
+    void iteration_body_t() {
         FieldView none = {nullptr, nullptr, 0};
-        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, p, tmp, none, none, none, A, 1));   // tmp = H_oe p
-        hop<P, EPI_MHAT, DOT_RHAT>(hop_args(0, tmp, v, p, none, rh, A, 1));        // v = p - k^2 H_eo tmp
-        fin<FIN_ALPHA>();                                                           // alpha = rho / (rh, v)
-        blas<P, OP_S_UPDATE>(A);                                                    // s = r - alpha v
-        hop<P, EPI_PLAIN, DOT_NONE>(hop_args(1, s, tmp, none, none, none, A, 1));   // tmp = H_oe s
-        hop<P, EPI_MHAT, DOT_TS>(hop_args(0, tmp, t, s, none, none, A, 1));        // t = s - k^2 H_eo tmp
-        fin<FIN_OMEGA>();                                                           // omega = (t,s)/(t,t)
-        blas<P, OP_XR_UPDATE>(A);                                                   // x, r; (rh,r), (r,r)
-        fin<FIN_RHO>();                                                             // beta, convergence
-        blas<P, OP_P_UPDATE>(A);                                                    // p = r + beta (p - omega v)
+        hop<P, EPI_PLAIN, DOT_NONE, CL>(hop_args(1, p, tmp, none, none, none, A, 1));   // tmp = T^-1 H_oe p
+        hop<P, EPI_MHAT, DOT_RHAT, CL>(hop_args(0, tmp, v, p, none, rh, A, 1));        // v = p - k^2 T^-1 H_eo tmp
+        fin<FIN_ALPHA>();                                                               // alpha = rho / (rh, v)
+        blas<P, OP_S_UPDATE>(A);                                                        // s = r - alpha v
+        hop<P, EPI_PLAIN, DOT_NONE, CL>(hop_args(1, s, tmp, none, none, none, A, 1));   // tmp = T^-1 H_oe s
+        hop<P, EPI_MHAT, DOT_TS, CL>(hop_args(0, tmp, t, s, none, none, A, 1));        // t = s - k^2 T^-1 H_eo tmp
+        fin<FIN_OMEGA>();                                                               // omega = (t,s)/(t,t)
+        blas<P, OP_XR_UPDATE>(A);                                                       // x, r; (rh,r), (r,r)
+        fin<FIN_RHO>();                                                                 // beta, convergence
+        blas<P, OP_P_UPDATE>(A);                                                        // p = r + beta (p - omega v)
+    }
+    void iteration_body() {
+        if (clov)
+            iteration_body_t<true>();
+        else
+            iteration_body_t<false>();
     }
 
     int build_loop_graph() {
@@ -312,8 +324,13 @@ struct Engine {
     void residual(bool skip_hop) {
         FieldView none = {nullptr, nullptr, 0};
         if (!skip_hop) {
-            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A, 2));
-            hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B, 2));
+            if (clov) {
+                hop<PF64, EPI_RESID, DOT_NORM, true>(hop_args(0, xo, re64, xe, be, none, A, 2));
+                hop<PF64, EPI_RESID, DOT_NORM, true>(hop_args(1, xe, ro64, xo, bo, none, B, 2));
+            } else {
+                hop<PF64, EPI_RESID, DOT_NORM>(hop_args(0, xo, re64, xe, be, none, A, 2));
+                hop<PF64, EPI_RESID, DOT_NORM>(hop_args(1, xe, ro64, xo, bo, none, B, 2));
+            }
         }
         fin<FIN_RESID>();
     }
@@ -326,22 +343,27 @@ struct Engine {
     }
 
     // One correction: inner solve of the normalised defect and FP64 accumulation.
-    int correction(bool r_is_eta) {
+    // With 2 kappa D = [[T_ee, -k H_eo], [-k H_oe, T_oo]] and r' the normalised defect:
+    //   (1 - k^2 T_ee^-1 H_eo T_oo^-1 H_oe) e_e = T_ee^-1 (r'_e + k H_eo T_oo^-1 r'_o),
+    //   e_o = T_oo^-1 r'_o + k T_oo^-1 H_oe e_e   (T = 1 without the clover term).
+    template <bool CL>
+    int correction_t(bool r_is_eta) {
         FieldView none = {nullptr, nullptr, 0};
-        conv(true, s, r_is_eta ? be : re64);
-        conv(true, ro, r_is_eta ? bo : ro64);
-        hop<P, EPI_AXPY_K, DOT_NORM>(hop_args(0, ro, r, s, none, none, A));  // r = r'_e + k H_eo r'_o
+        conv(true, s, r_is_eta ? be : re64, 0);
+        conv(true, ro, r_is_eta ? bo : ro64, 1, CL);                                  // ro = T_oo^-1 r'_o
+        hop<P, EPI_RHS, DOT_NORM, CL>(hop_args(0, ro, r, s, none, none, A));         // r = T_ee^-1 (r'_e + k H_eo ro)
         blas<P, OP_INIT>(A, 0);
         DDP_CUDA(ctx, cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), ctx->stream));
         fin<FIN_INIT>();
         DDP_CUDA(ctx, cudaGetLastError());
         int rc = run_inner();
         if (rc) return rc;
-        hop<P, EPI_AXPY_K, DOT_NONE>(hop_args(1, xi, tmp, ro, none, none, A));  // e'_o = r'_o + k H_oe e'_e
+        hop<P, EPI_AXPY_K, DOT_NONE, CL>(hop_args(1, xi, tmp, ro, none, none, A));  // e_o = ro + k T^-1 H_oe e_e
         conv(false, xi, xe);
         conv(false, tmp, xo);
         return DDP_OK;
     }
+    int correction(bool r_is_eta) { return clov ? correction_t<true>(r_is_eta) : correction_t<false>(r_is_eta); }
 
     void drop_graph() {
         if (loop_exec) cudaGraphExecDestroy(loop_exec);
@@ -355,6 +377,8 @@ struct Engine {
     int run(std::vector<Job> &jobs, std::vector<JobInfo> &infos) {
         const EngineParams &prm = ctx->prm;
         make_plan(jobs, prec, prm, plan);
+        clov = false;
+        for (auto &j : jobs) clov = clov || j.clov;
         DDP_CUDA(ctx, ctx->ws.reserve(bytes_needed(plan.nfield, plan.npart, (int)plan.items.size(), plan.nsolve)));
         carve(ctx->ws, plan.nfield, plan.npart, (int)plan.items.size(), plan.nsolve);
         std::vector<SolveState> states(plan.nsolve);
@@ -456,12 +480,18 @@ int apply_dirac_impl(ddp_ctx *ctx, const Job &job, const double *psi, double *ou
     h.in = io;
     h.out = oe;
     h.v1 = ie;
-    launch_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+    auto dirac = [&]() {
+        if (job.clov)
+            launch_hop<P, EPI_DIRAC, DOT_NONE, true>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+        else
+            launch_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+    };
+    dirac();
     h.p = 1;
     h.in = ie;
     h.out = oo;
     h.v1 = io;
-    launch_hop<P, EPI_DIRAC, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
+    dirac();
     k_unpack_low<P><<<nb, 256, 0, st>>>(pa, oe, oo);
     ctx->launches += 4;
     DDP_CUDA(ctx, cudaGetLastError());

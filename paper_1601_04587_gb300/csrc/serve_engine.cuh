@@ -123,6 +123,7 @@ struct Server : ServerBase {
         std::vector<Job> jobs;
         for (uint64_t t : active) jobs.push_back(reqs[t].job);
         make_plan(jobs, prec, ctx->prm, eng.plan);
+        eng.clov = false;  // serving refuses the clover term (ddp_submit)
         std::vector<SolveState> states(eng.plan.nsolve);
         for (size_t i = 0; i < active.size(); i++) {
             Req &r = reqs[active[i]];

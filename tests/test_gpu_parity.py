@@ -201,8 +201,8 @@ def test_invalid_arguments(ddp, ctx, field):
     n = int(np.prod(BOXES[1][1]))
     S = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
     with pytest.raises(ddp.DDPError) as ei:
-        ddp.ddp_solve_propagator(ctx, did, 0.12, 0.5, (7, 0, 0, 0), 1e-10, 0, S)
-    assert ei.value.status == ddp.DDP_ERR_UNSUPPORTED      # clover term
+        ddp.ddp_solve_propagator(ctx, did, 0.12, float("nan"), (7, 0, 0, 0), 1e-10, 0, S)
+    assert ei.value.status == ddp.DDP_ERR_INVALID_ARG      # clover coefficient not finite
     with pytest.raises(ddp.DDPError) as ei:
         ddp.ddp_solve_propagator(ctx, did, 0.12, 0.0, (3, 0, 0, 0), 1e-10, 0, S)
     assert ei.value.status == ddp.DDP_ERR_INVALID_ARG      # source outside the domain
@@ -558,3 +558,76 @@ def test_propagator_series_rejects_non_nested(ddp, ctx, field):
     assert ei.value.status == ddp.DDP_ERR_INVALID_ARG
     ddp.ddp_free_domain(ctx, a)
     ddp.ddp_free_domain(ctx, b)
+
+
+# ----------------------------------------------------- clover (O(a)-improved) operator
+
+CSW = 1.7
+
+
+@pytest.mark.parametrize("box", BOXES[:5])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 1e-6), (2, 4e-3), (3, 3e-2)])
+def test_apply_dirac_clover(ddp, ctx, field, box, prec, tol):
+    """D_Gamma with the clover term against the oracle, every storage format."""
+    U, gid = field
+    o, e = box
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    psi = synth.random_spinor(3, n, 19)
+    ref = oracle.apply_dirac(U, LAT, AP, o, e, 0.1315, psi, csw=CSW)
+    out = torch.zeros((3, n, 4, 3), dtype=torch.complex128, device="cuda")
+    ddp.ddp_apply_dirac(ctx, did, 0.1315, torch.from_numpy(psi).cuda(), out, 3, prec, csw=CSW)
+    errs = _col_errors(out.cpu().numpy(), ref)
+    assert max(errs) < tol, errs
+    # the clover part alone (D(c_sw) - D(0)) is right too, not only the total
+    plain = torch.zeros_like(out)
+    ddp.ddp_apply_dirac(ctx, did, 0.1315, torch.from_numpy(psi).cuda(), plain, 3, prec)
+    diff = (out - plain).cpu().numpy()
+    want = ref - oracle.apply_dirac(U, LAT, AP, o, e, 0.1315, psi)
+    assert max(_col_errors(diff, want)) < 50 * tol
+    ddp.ddp_free_domain(ctx, did)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("box,src", [(BOXES[0], (0, 0, 0, 0)), (BOXES[1], (7, 1, 2, 3)), (BOXES[3], (4, 3, 1, 0))])
+def test_solve_propagator_clover(ddp, ctx, field, prec, box, src):
+    """S^(i) of the O(a)-improved operator (even-odd Schur complement with T^-1 on both
+    parities) against the oracle's solve of the unpreconditioned D_Gamma."""
+    U, gid = field
+    o, e = box
+    kappa, csw = 0.12, 1.0
+    did = ddp.ddp_set_domain(ctx, gid, o, e)
+    n = int(np.prod(e))
+    ref, _, rr, st = oracle.propagator(U, LAT, AP, o, e, kappa, src, tol=1e-12, csw=csw)
+    assert st == 0
+    S = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
+    rc, info = ddp.ddp_solve_propagator(ctx, did, kappa, csw, src, 1e-10, prec, S)
+    assert rc == ddp.DDP_OK, ddp.info_dict(info)
+    assert info.max_rel_residual <= 1e-10
+    errs = _col_errors(S.cpu().numpy(), ref)
+    assert max(errs) < COL_TOL, errs
+    ddp.ddp_free_domain(ctx, did)
+
+
+def test_batch_mixing_clover_and_plain_requests(ddp, ctx, field):
+    """One batch with a plain Wilson request, two clover requests of different kappa
+    and one of a different c_sw: every column against the oracle."""
+    U, gid = field
+    cases = [((6, 0, 0, 0), (4, 4, 4, 6), (7, 1, 2, 3), 0.12, 0.0),
+             ((6, 0, 0, 0), (4, 4, 4, 6), (7, 1, 2, 3), 0.12, 1.0),
+             ((0, 0, 0, 0), LAT, (3, 2, 2, 4), 0.115, 1.0),
+             ((2, 3, 0, 5), (5, 4, 2, 2), (4, 3, 1, 0), 0.12, 1.5)]
+    dids, outs, reqs = [], [], []
+    for o, e, src, kappa, csw in cases:
+        d = ddp.ddp_set_domain(ctx, gid, o, e)
+        out = torch.zeros((12, int(np.prod(e)), 4, 3), dtype=torch.complex128, device="cuda")
+        dids.append(d)
+        outs.append(out)
+        reqs.append(ddp.make_req(d, kappa, src, 1e-10, out, csw=csw))
+    rc, infos = ddp.ddp_solve_batch(ctx, reqs, ddp.DDP_PREC_MIXED_FP32)
+    assert rc == ddp.DDP_OK
+    for (o, e, src, kappa, csw), out in zip(cases, outs):
+        ref, *_ = oracle.propagator(U, LAT, AP, o, e, kappa, src, tol=1e-12, csw=csw)
+        assert max(_col_errors(out.cpu().numpy(), ref)) < COL_TOL, (o, e, kappa, csw)
+    for d in dids:
+        ddp.ddp_free_domain(ctx, d)
