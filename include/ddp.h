@@ -339,6 +339,63 @@ long ddp_kernel_launches(const ddp_ctx *ctx);
 /* Clears the serving state (pending and finished requests). */
 int ddp_serve_reset(ddp_ctx *ctx);
 
+/* ---- projector-cut factorization (Sec. 5) ------------------------------------
+ * The factorized propagator of Eq. approxlong with the projector P = sum_i phi_i
+ * phi_i^+ on N_m orthonormal vectors inserted at the cut (Eq. proj, approxlong2):
+ *   S~(y, x) = -sum_i [D^-1_{G*} D_dG* phi_i](y) [phi_i^+ D^-1_{Gbar}](x).
+ * A caller builds it from these calls and the solves above:
+ *   phi  = ddp_inverse_iteration on the thick slice Omega at the cut,
+ *   u_i  = D^-1_{Gbar} g5 phi_i      (ddp_embed with gamma5 = 1, ddp_solve_sources),
+ *   w_i  = D^-1_{G*} sigma_i,  sigma_i = ddp_boundary_source(Omega -> G*, phi_i),
+ *   pion:    M = ddp_gram_slices(Gbar, u), M~ = ddp_gram_slices(G*, w),
+ *            ddp_projected_pion(M~, M)                         (Eq. Bpions, fullfactpi),
+ *   nucleon: X = ddp_colourless_slices(Gbar, u, form 1), Y = ddp_colourless_slices(G*, w,
+ *            form 2), ddp_projected_nucleon(X, Y)              (Eq. W0tbary).
+ * Fields: [m][n_sites][4][3] complex in domain-local order, host or device memory
+ * (detected per pointer); every call returns when its output is complete. */
+
+/* V <- the orthonormal basis of span(V) that Gram-Schmidt in column order gives
+ * (Cholesky QR, twice, in FP64).  DDP_ERR_INVALID_ARG if the columns are linearly
+ * dependent or m > 12 n_sites. */
+int ddp_orthonormalize(ddp_ctx *ctx, int domain_id, double *V, int m);
+
+/* Subspace inverse iteration of the Dirichlet operator of the domain (Sec. 5: 10
+ * iterations on random vectors): V <- orthonormalize(V), then `iters` times
+ * V <- orthonormalize(D_Gamma^-1 V), each solve to the relative residual tol in
+ * `precision` (ddp_solve_sources).  V: m columns in, the orthonormal vectors out;
+ * info: as ddp_solve_sources for the last solve (may be NULL).  Returns
+ * DDP_ERR_NOT_CONVERGED (V still written) if a solve missed tol. */
+int ddp_inverse_iteration(ddp_ctx *ctx, int domain_id, double kappa, double csw, double *V, int m, int iters,
+                          double tol, int precision, ddp_solve_info *info);
+
+/* out = E psi (times gamma_5 when gamma5 != 0): the ncol columns of the `from`
+ * domain extended by zero to the `to` domain, which must contain it. */
+int ddp_embed(ddp_ctx *ctx, int domain_from, const double *psi, int domain_to, double *out, int ncol, int gamma5);
+
+/* M[t][i][j] = sum_{x vec at global time t} sum_{spin, colour} conj(A_i(x)) A_j(x)
+ * for the m columns of a domain: the time-slice sums of the pion blocks B_ij of
+ * Eq. Bpions.  M_out: L0 x m x m complex; slices outside the domain are zero. */
+int ddp_gram_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, double *M_out);
+
+/* X[t][i][j][k][alpha] = sum_{x vec at time t} B[s_i, s_j, s_k; x]_alpha, the
+ * colourless spinors B[s_i, s_j, s_k; x]_alpha = eps^{abc} (s_i^a)^T C g5 s_j^b (s_k^c)_alpha
+ * of Eq. W0tbary (C = i g0 g2) with s_i = A_i (form 0), g5 conj(A_i) (form 1: the
+ * spinor of the row phi_i^+ D^-1 when A_i = D^-1 g5 phi_i) or -A_i (form 2).
+ * X_out: L0 x m^3 x 4 complex.  m <= 32 (else DDP_ERR_UNSUPPORTED). */
+int ddp_colourless_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, int form, double *X_out);
+
+/* C[y0][x0] = (1/L^3) sum_ij Mt[y0][i][j] M[x0][j][i] = (1/L^3) sum_{x vec, y vec} W~(y, x)
+ * of Eq. fullfactpi.  Mt, M: L0 x m x m complex; C_out: L0 x L0 complex. */
+int ddp_projected_pion(ddp_ctx *ctx, int L0, int m, const double *Mt, const double *M, double spatial_volume,
+                       double *C_out);
+
+/* C[y0][x0] = sum_{x vec, y vec} [W~_N1 - W~_N2](y, x) = sum_ijk [X_jik(x0) - X_kij(x0)]^T
+ * P- Y_ijk(y0), P- = (1 - g0)/2: the nucleon contractions of Sec. 4 with S~
+ * substituted (Eq. W0tbary; the paper prints -g5 P- between the spinors, which
+ * corresponds to an x-side spinor with an extra -g5).  X, Y: L0 x m^3 x 4 complex
+ * from ddp_colourless_slices; C_out: L0 x L0 complex. */
+int ddp_projected_nucleon(ddp_ctx *ctx, int L0, int m, const double *X, const double *Y, double *C_out);
+
 /* ---- allocation-free contraction ------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * must not allocate device memory, for instance code running under another

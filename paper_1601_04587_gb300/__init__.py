@@ -97,6 +97,13 @@ def lib():
             "ddp_autotune": ([vp, i, d, i, i, i, i4, ctypes.POINTER(ctypes.c_float)], i),
             "ddp_propagator_series": ([vp, i, i4, d, d, i4, d, i, ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp,
                                        ctypes.POINTER(ddp_solve_info)], i),
+            "ddp_orthonormalize": ([vp, i, vp, i], i),
+            "ddp_inverse_iteration": ([vp, i, d, d, vp, i, i, d, i, ctypes.POINTER(ddp_solve_info)], i),
+            "ddp_embed": ([vp, i, vp, i, vp, i, i], i),
+            "ddp_gram_slices": ([vp, i, vp, i, vp], i),
+            "ddp_colourless_slices": ([vp, i, vp, i, i, vp], i),
+            "ddp_projected_pion": ([vp, i, i, vp, vp, d, vp], i),
+            "ddp_projected_nucleon": ([vp, i, i, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -273,6 +280,42 @@ def ddp_propagator_series(ctx, domain_ids, kappa, src, tol, precision, S_out=Non
                                      int(contract_mask), _ptr(C_out), infos)
     _check(ctx, rc, "ddp_propagator_series", allow=(DDP_ERR_NOT_CONVERGED,))
     return rc, list(infos)
+
+
+def ddp_orthonormalize(ctx, domain_id, V, m):
+    return _check(ctx, lib().ddp_orthonormalize(ctx, int(domain_id), _ptr(V), int(m)), "ddp_orthonormalize")
+
+
+def ddp_inverse_iteration(ctx, domain_id, kappa, V, m, iters, tol, precision, csw=0.0):
+    info = ddp_solve_info()
+    rc = lib().ddp_inverse_iteration(ctx, int(domain_id), float(kappa), float(csw), _ptr(V), int(m), int(iters),
+                                     float(tol), int(precision), ctypes.byref(info))
+    _check(ctx, rc, "ddp_inverse_iteration", allow=(DDP_ERR_NOT_CONVERGED,))
+    return rc, info
+
+
+def ddp_embed(ctx, domain_from, psi, domain_to, out, ncol, gamma5=False):
+    return _check(ctx, lib().ddp_embed(ctx, int(domain_from), _ptr(psi), int(domain_to), _ptr(out), int(ncol),
+                                       1 if gamma5 else 0), "ddp_embed")
+
+
+def ddp_gram_slices(ctx, domain_id, A, m, M_out):
+    return _check(ctx, lib().ddp_gram_slices(ctx, int(domain_id), _ptr(A), int(m), _ptr(M_out)), "ddp_gram_slices")
+
+
+def ddp_colourless_slices(ctx, domain_id, A, m, form, X_out):
+    return _check(ctx, lib().ddp_colourless_slices(ctx, int(domain_id), _ptr(A), int(m), int(form), _ptr(X_out)),
+                  "ddp_colourless_slices")
+
+
+def ddp_projected_pion(ctx, L0, m, Mt, M, spatial_volume, C_out):
+    return _check(ctx, lib().ddp_projected_pion(ctx, int(L0), int(m), _ptr(Mt), _ptr(M), float(spatial_volume),
+                                                _ptr(C_out)), "ddp_projected_pion")
+
+
+def ddp_projected_nucleon(ctx, L0, m, X, Y, C_out):
+    return _check(ctx, lib().ddp_projected_nucleon(ctx, int(L0), int(m), _ptr(X), _ptr(Y), _ptr(C_out)),
+                  "ddp_projected_nucleon")
 
 
 def ddp_factorized_correlator(ctx, T_A, nvar_A, T_B, nvar_B, L0, spatial_volume, C_out):

@@ -119,6 +119,7 @@ struct ddp_ctx {
     ddp::Arena ws;        // solver workspace
     ddp::Arena scratch;   // staging of host buffers, contraction partials
     ddp::Arena results;   // device-resident propagators and series terms of ddp_propagator_series
+    ddp::Arena aux;       // partial sums of the projector-cut kernels
     cudaStream_t copy_stream = nullptr;  // device-to-host copies overlapped with compute (created on first use)
     void *serve = nullptr;
     // instrumentation: per-kernel-class launch counts of the last solve

@@ -1,0 +1,166 @@
+"""GPU projector-cut factorization (Sec. 5) against the oracle, through the C ABI.
+
+Pieces: orthonormalization, inverse-iteration modes, time-slice Gram blocks
+(Eq. Bpions), colourless spinors (Eq. W0tbary), the two projected correlators;
+then the whole pion and nucleon pipeline from the modes to C(y0, x0).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import projector
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+AP = oracle.BC_ANTIPERIODIC
+L = (12, 4, 4, 4)
+KAPPA = 0.12
+GBAR = ((0, 0, 0, 0), (8, 4, 4, 4))    # slices 0..7   (x0cut = 6, Delta = 2)
+GSTAR = ((6, 0, 0, 0), (5, 4, 4, 4))   # slices 6..10
+OMEGA = ((4, 0, 0, 0), (4, 4, 4, 4))   # slices 4..7
+VOL3 = L[1] * L[2] * L[3]
+CORR_TOL = 1e-7
+
+
+@pytest.fixture(scope="module")
+def ddp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_04587_gb300 import build
+    build.build()
+    import paper_1601_04587_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def env(ddp):
+    U = synth.gauge_field(L, seed=41)
+    ctx = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    gid = ddp.ddp_load_gauge(ctx, torch.from_numpy(U).cuda(), L, ddp.DDP_BC_ANTIPERIODIC)
+    doms = {name: ddp.ddp_set_domain(ctx, gid, *box) for name, box in
+            (("bar", GBAR), ("star", GSTAR), ("omega", OMEGA))}
+    doms["gid"] = gid
+    yield U, ctx, doms
+    ddp.ddp_destroy(ctx)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_orthonormalize_matches_oracle(ddp, env):
+    U, ctx, doms = env
+    n = oracle.box_sites(OMEGA[1])
+    V = synth.random_spinor(8, n, 3)
+    Vd = _dev(V)
+    ddp.ddp_orthonormalize(ctx, doms["omega"], Vd, 8)
+    assert np.abs(Vd.cpu().numpy() - projector.orthonormalize(V)).max() < 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_inverse_iteration_matches_oracle(ddp, env, prec):
+    U, ctx, doms = env
+    n = oracle.box_sites(OMEGA[1])
+    V0 = synth.random_spinor(6, n, 7)
+    want = projector.inverse_iteration(U, L, AP, *OMEGA, KAPPA, V0, 3)
+    Vd = _dev(V0)
+    rc, _ = ddp.ddp_inverse_iteration(ctx, doms["omega"], KAPPA, Vd, 6, 3, 1e-11, prec)
+    assert rc == ddp.DDP_OK
+    got = Vd.cpu().numpy()
+    assert max(_rel(got[c], want[c]) for c in range(6)) < 1e-8
+
+
+def test_gram_slices_matches_oracle(ddp, env):
+    U, ctx, doms = env
+    n = oracle.box_sites(GBAR[1])
+    A = synth.random_spinor(20, n, 11)
+    M = torch.zeros((L[0], 20, 20), dtype=torch.complex128, device="cuda")
+    ddp.ddp_gram_slices(ctx, doms["bar"], _dev(A), 20, M)
+    want = projector.gram_slices(L, *GBAR, A)
+    assert _rel(M.cpu().numpy(), want) < 1e-13
+    # a domain that wraps in time puts its slices at their global times (host buffers)
+    wrap = ((10, 1, 0, 0), (4, 2, 4, 4))
+    did = ddp.ddp_set_domain(ctx, doms["gid"], *wrap)
+    M2 = np.zeros((L[0], 20, 20), dtype=np.complex128)
+    A2 = synth.random_spinor(20, oracle.box_sites(wrap[1]), 12)
+    ddp.ddp_gram_slices(ctx, did, A2, 20, M2)
+    assert _rel(M2, projector.gram_slices(L, *wrap, A2)) < 1e-13
+    ddp.ddp_free_domain(ctx, did)
+
+
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_colourless_slices_matches_oracle(ddp, env, form):
+    U, ctx, doms = env
+    n = oracle.box_sites(GSTAR[1])
+    A = synth.random_spinor(5, n, 13)
+    X = torch.zeros((L[0], 5, 5, 5, 4), dtype=torch.complex128, device="cuda")
+    ddp.ddp_colourless_slices(ctx, doms["star"], _dev(A), 5, form, X)
+    g5 = oracle.gamma()[4]
+    s = {0: A, 1: np.einsum("ab,mnbc->mnac", g5, np.conj(A)), 2: -A}[form]
+    want = projector.colourless_spinors(L, *GSTAR, s)
+    assert _rel(X.cpu().numpy(), want) < 1e-12
+
+
+def test_colourless_slices_rejects_too_many_columns(ddp, env):
+    U, ctx, doms = env
+    n = oracle.box_sites(OMEGA[1])
+    A = torch.zeros((33, n, 4, 3), dtype=torch.complex128, device="cuda")
+    X = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    with pytest.raises(ddp.DDPError) as ei:
+        ddp.ddp_colourless_slices(ctx, doms["omega"], A, 33, 0, X)
+    assert ei.value.status == ddp.DDP_ERR_UNSUPPORTED
+
+
+def test_projected_pion_and_nucleon_pipeline(ddp, env):
+    """Modes on Omega, u_i = D^-1_{Gbar} g5 phi_i, w_i = D^-1_{G*} sigma_i, the pion
+    from the Gram blocks and the nucleon from the colourless spinors, all on the GPU,
+    against the oracle's route."""
+    U, ctx, doms = env
+    m = 6
+    n_o, n_b, n_s = (oracle.box_sites(b[1]) for b in (OMEGA, GBAR, GSTAR))
+    V0 = synth.random_spinor(m, n_o, 21)
+    phi = projector.inverse_iteration(U, L, AP, *OMEGA, KAPPA, V0, 2)
+    u_ref, w_ref = projector.factorized_vectors(U, L, AP, KAPPA, GBAR, GSTAR, OMEGA, phi)
+    M_ref = projector.gram_slices(L, *GBAR, u_ref)
+    Mt_ref = projector.gram_slices(L, *GSTAR, w_ref)
+    Cpi_ref = projector.projected_pion(Mt_ref, M_ref, VOL3)
+    g5 = oracle.gamma()[4]
+    X_ref = projector.colourless_spinors(L, *GBAR, np.einsum("ab,mnbc->mnac", g5, np.conj(u_ref)))
+    Y_ref = projector.colourless_spinors(L, *GSTAR, -w_ref)
+    Cn_ref = projector.projected_nucleon(X_ref, Y_ref)
+
+    dphi = _dev(V0)
+    rc, _ = ddp.ddp_inverse_iteration(ctx, doms["omega"], KAPPA, dphi, m, 2, 1e-11, ddp.DDP_PREC_MIXED_FP32)
+    assert rc == ddp.DDP_OK
+    src = torch.zeros((m, n_b, 4, 3), dtype=torch.complex128, device="cuda")
+    ddp.ddp_embed(ctx, doms["omega"], dphi, doms["bar"], src, m, gamma5=True)
+    u = torch.zeros_like(src)
+    rc, _ = ddp.ddp_solve_sources(ctx, doms["bar"], KAPPA, 0.0, src, m, 1e-11, ddp.DDP_PREC_MIXED_FP32, u)
+    assert rc == ddp.DDP_OK
+    sigma = torch.zeros((m, n_s, 4, 3), dtype=torch.complex128, device="cuda")
+    ddp.ddp_boundary_source(ctx, doms["omega"], dphi, doms["star"], sigma, m)
+    w = torch.zeros_like(sigma)
+    rc, _ = ddp.ddp_solve_sources(ctx, doms["star"], KAPPA, 0.0, sigma, m, 1e-11, ddp.DDP_PREC_MIXED_FP32, w)
+    assert rc == ddp.DDP_OK
+    assert _rel(u.cpu().numpy(), u_ref) < 1e-8 and _rel(w.cpu().numpy(), w_ref) < 1e-8
+    M = torch.zeros((L[0], m, m), dtype=torch.complex128, device="cuda")
+    Mt = torch.zeros_like(M)
+    ddp.ddp_gram_slices(ctx, doms["bar"], u, m, M)
+    ddp.ddp_gram_slices(ctx, doms["star"], w, m, Mt)
+    Cpi = torch.zeros((L[0], L[0]), dtype=torch.complex128, device="cuda")
+    ddp.ddp_projected_pion(ctx, L[0], m, Mt, M, VOL3, Cpi)
+    assert _rel(Cpi.cpu().numpy(), Cpi_ref) < CORR_TOL
+    X = torch.zeros((L[0], m, m, m, 4), dtype=torch.complex128, device="cuda")
+    Y = torch.zeros_like(X)
+    ddp.ddp_colourless_slices(ctx, doms["bar"], u, m, 1, X)
+    ddp.ddp_colourless_slices(ctx, doms["star"], w, m, 2, Y)
+    Cn = torch.zeros((L[0], L[0]), dtype=torch.complex128, device="cuda")
+    ddp.ddp_projected_nucleon(ctx, L[0], m, X, Y, Cn)
+    assert _rel(Cn.cpu().numpy(), Cn_ref) < CORR_TOL
