@@ -41,6 +41,7 @@ THICK = synth.SLAB_THICKNESS
 # domains), 0.1400 is the largest value on a 0.005 grid at which every domain
 # of the workload converges.
 KAPPA = 0.1400
+CSW = 0.0        # clover coefficient of the operator (0: plain Wilson); --csw
 TOL = 1e-10
 SRC = (0, 0, 0, 0)
 METRIC = "domain-propagator solves/s (12 columns, true FP64 residual 1e-10)"
@@ -162,7 +163,7 @@ class Workload:
         gid = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
         dids = [ddp.ddp_set_domain(ctx, gid, b.origin, b.extent) for b in self.bx]
         rc, self.infos = ddp.ddp_propagator_series(ctx, dids, KAPPA, SRC, TOL, self.prec, S_out=outs, T_out=terms,
-                                                   contract_mask=CONTRACT_MASK, C_out=C)
+                                                   contract_mask=CONTRACT_MASK, C_out=C, csw=CSW)
         for d in dids:
             ddp.ddp_free_domain(ctx, d)
         ddp.ddp_free_gauge(ctx, gid)
@@ -232,7 +233,7 @@ def oracle_columns(U, kappa, boxes_, tol):
         n = b.n_sites
         eta = np.zeros((1, n, 4, 3), dtype=np.complex128)
         eta[0, oracle.local_index(L, b.origin, b.extent, SRC), 0, 0] = 1.0
-        psi, _, _, _ = oracle.solve(U, L, oracle.BC_ANTIPERIODIC, b.origin, b.extent, kappa, eta, tol=tol)
+        psi, _, _, _ = oracle.solve(U, L, oracle.BC_ANTIPERIODIC, b.origin, b.extent, kappa, eta, tol=tol, csw=CSW)
         cols.append(psi[0])
     return time.perf_counter() - t0, cols
 
@@ -287,7 +288,7 @@ def parity_block(ddp, torch, ctx, wl, U, cpu_cols):
         l = oracle.local_index(L, b.origin, b.extent, SRC)
         for c in range(12):
             eta[c, l, c // 3, c % 3] = 1.0
-        r = eta - oracle.apply_dirac(U, L, oracle.BC_ANTIPERIODIC, b.origin, b.extent, KAPPA, S)
+        r = eta - oracle.apply_dirac(U, L, oracle.BC_ANTIPERIODIC, b.origin, b.extent, KAPPA, S, csw=CSW)
         rr = [float(np.linalg.norm(r[c]) / np.linalg.norm(eta[c])) for c in range(12)]
         out["propagators"].append({"domain": list(b.extent), "oracle_max_rel_residual": max(rr)})
         C = wl.C[i].cpu().numpy()
@@ -417,8 +418,8 @@ def run_gpu(args):
                                                            "bf16": "bf16"}[args.precision],
         "data": "synthetic (seeded SU(3) field, plaquette 0.59)",
         "config": {"workload": f"48x24^3 nested time slabs 8/16/24 + full lattice, 12-column point-source "
-                               f"propagators, kappa {KAPPA}, tol {TOL}",
-                   "lattice": list(L), "kappa": KAPPA, "kappa_stated": 0.155, "tol": TOL,
+                               f"propagators, kappa {KAPPA}, tol {TOL}" + (f", clover c_sw {CSW}" if CSW else ""),
+                   "lattice": list(L), "kappa": KAPPA, "kappa_stated": 0.155, "tol": TOL, "csw": CSW,
                    "precision": f"mixed: FP32 inner on {args.precision} storage, FP64 defect correction"
                    if prec else "fp64",
                    "l2": "inputs larger than L2 (links 0.38 GB FP64, propagators 3.1 GB)",
@@ -472,6 +473,8 @@ def run_other(args):
         res = workloads.multilevel_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
     elif args.workload == "next":
         res = workloads.next_rows_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
+    elif args.workload == "projector":
+        res = workloads.projector_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
     else:
         res = workloads.serve_workload(ddp, torch, ctx, synth, prec)
     res["clocks"] = clocks.stop()
@@ -553,7 +556,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", default="slabs", choices=["slabs", "batch", "multilevel", "serve", "next", "hop"],
+    ap.add_argument("--workload", default="slabs", choices=["slabs", "batch", "multilevel", "serve", "next", "hop",
+                                                         "projector"],
                     help="slabs: the benchmark line; the others print their own measurement line")
     ap.add_argument("--lattice", type=int, nargs=4, default=[32, 24, 24, 24], help="--workload hop: lattice")
     ap.add_argument("--kernel", default="all", help="--workload hop: plain, schur_rhat, schur_ts or all")
@@ -561,14 +565,21 @@ def main():
     ap.add_argument("--iters", type=int, default=20, help="--workload hop: timed launches per kernel")
     ap.add_argument("--param", action="append", default=[],
                     help="solver parameter name=value passed to ddp_set_param (repeatable)")
+    ap.add_argument("--kappa", type=float, default=None, help="slabs: kappa (default 0.14)")
+    ap.add_argument("--csw", type=float, default=0.0, help="slabs: clover coefficient c_sw (default 0)")
     ap.add_argument("--no-conditional", action="store_true",
                     help="run the inner loop as host-polled graph chunks (profilers see its kernels)")
     args = ap.parse_args()
+    global KAPPA, CSW
+    if args.kappa is not None:
+        KAPPA = args.kappa
+    CSW = args.csw
     long_steps = args.workload == "multilevel"
+    short = args.workload in ("next", "projector")
     if args.steps is None:
-        args.steps = 1 if long_steps else (2 if args.workload == "next" else 5)
+        args.steps = 1 if long_steps else (2 if short else 5)
     if args.warmup is None:
-        args.warmup = 0 if long_steps else (1 if args.workload == "next" else 3)
+        args.warmup = 0 if long_steps else (1 if short else 3)
     if args.warmup < 3 and args.workload == "slabs" and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -207,6 +207,89 @@ def next_rows_workload(ddp, torch, ctx, synth, precision, steps=2, warmup=1, L=N
             "max_rel_residuals": res, "steps": steps, "warmup": warmup}
 
 
+# ------------------------------------------------ projector-cut factorization
+
+def projector_workload(ddp, torch, ctx, synth, precision, nm=24, iters=10, steps=1, warmup=1, L=None, x0_cut=24,
+                       delta=8):
+    """48 x 24^3 lattice, kappa 0.140, the projector cut of Sec. 5 at x0_cut = 24 with
+    Delta = 8: Gamma-bar_0 = time slices [0, 32), Gamma*_0 = [24, 48), Omega = [16, 32).
+    Per step: nm orthonormal vectors by `iters` inverse iterations of D_Omega on seeded
+    random vectors, u_i = D^-1_{Gbar} g5 phi_i, w_i = D^-1_{G*} sigma_i, the pion
+    (time-slice Gram blocks, Eq. fullfactpi) and the nucleon (colourless spinors, Eq.
+    W0tbary) for every (y0, x0).  Solves: mixed precision to 1e-10."""
+    L = tuple(L or synth.SLAB_LATTICE)
+    kappa = 0.140
+    U = synth.gauge_field_torch(L, seed=synth.SEED_GAUGE, device="cuda")
+    bar = ((0, 0, 0, 0), (x0_cut + delta, L[1], L[2], L[3]))
+    star = ((x0_cut, 0, 0, 0), (L[0] - x0_cut, L[1], L[2], L[3]))
+    omega = ((x0_cut - delta, 0, 0, 0), (2 * delta, L[1], L[2], L[3]))
+    nb, ns, no = (int(np.prod(b[1])) for b in (bar, star, omega))
+    V0 = torch.from_numpy(synth.random_spinor(nm, no, synth.SEED_NOISE0 + 7)).cuda()
+    phi = torch.empty_like(V0)
+    src = torch.empty((nm, nb, 4, 3), dtype=torch.complex128, device="cuda")
+    u = torch.empty_like(src)
+    sig = torch.empty((nm, ns, 4, 3), dtype=torch.complex128, device="cuda")
+    w = torch.empty_like(sig)
+    M = torch.empty((L[0], nm, nm), dtype=torch.complex128, device="cuda")
+    Mt = torch.empty_like(M)
+    X = torch.empty((L[0], nm, nm, nm, 4), dtype=torch.complex128, device="cuda")
+    Y = torch.empty_like(X)
+    Cpi = torch.empty((L[0], L[0]), dtype=torch.complex128, device="cuda")
+    Cn = torch.empty_like(Cpi)
+    gid = ddp.ddp_load_gauge(ctx, U, L, ddp.DDP_BC_ANTIPERIODIC)
+    d_bar, d_star, d_om = (ddp.ddp_set_domain(ctx, gid, *b) for b in (bar, star, omega))
+    times = {}
+
+    def stage(name, fn):
+        a, b = _events(torch)
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        times[name] = times.get(name, 0.0) + a.elapsed_time(b) / 1e3
+        return r
+
+    def step():
+        phi.copy_(V0)
+        rc1, _ = stage("modes", lambda: ddp.ddp_inverse_iteration(ctx, d_om, kappa, phi, nm, iters, 1e-10, precision))
+        stage("sources", lambda: (ddp.ddp_embed(ctx, d_om, phi, d_bar, src, nm, gamma5=True),
+                                  ddp.ddp_boundary_source(ctx, d_om, phi, d_star, sig, nm)))
+        rc2, _ = stage("solves", lambda: ddp.ddp_solve_sources(ctx, d_bar, kappa, 0.0, src, nm, 1e-10, precision, u))
+        rc3, _ = stage("solves", lambda: ddp.ddp_solve_sources(ctx, d_star, kappa, 0.0, sig, nm, 1e-10, precision, w))
+        stage("pion", lambda: (ddp.ddp_gram_slices(ctx, d_bar, u, nm, M), ddp.ddp_gram_slices(ctx, d_star, w, nm, Mt),
+                               ddp.ddp_projected_pion(ctx, L[0], nm, Mt, M, L[1] * L[2] * L[3], Cpi)))
+        stage("nucleon", lambda: (ddp.ddp_colourless_slices(ctx, d_bar, u, nm, 1, X),
+                                  ddp.ddp_colourless_slices(ctx, d_star, w, nm, 2, Y),
+                                  ddp.ddp_projected_nucleon(ctx, L[0], nm, X, Y, Cn)))
+        return rc1 or rc2 or rc3
+
+    for _ in range(warmup):
+        step()
+    times.clear()
+    a, b = _events(torch)
+    torch.cuda.synchronize()
+    a.record()
+    rc = 0
+    for _ in range(steps):
+        rc = rc or step()
+    b.record()
+    torch.cuda.synchronize()
+    secs = a.elapsed_time(b) / 1e3
+    for d in (d_bar, d_star, d_om):
+        ddp.ddp_free_domain(ctx, d)
+    ddp.ddp_free_gauge(ctx, gid)
+    # 10 iterations of nm columns on Omega, nm columns on each of Gamma-bar and Gamma*
+    col_solves = iters * nm + 2 * nm
+    return {"workload": f"48x24^3 projector cut (Sec. 5): x0_cut {x0_cut}, Delta {delta}, {nm} modes from {iters} "
+                        f"inverse iterations on t in [{x0_cut - delta}, {x0_cut + delta}), u on [0, {x0_cut + delta}), "
+                        f"w on [{x0_cut}, {L[0]}), pion and nucleon for every (y0, x0), kappa {kappa}",
+            "s_per_step": secs / steps, "s_per_stage": {k: v / steps for k, v in times.items()},
+            "column_solves_per_step": col_solves, "status": rc, "steps": steps, "warmup": warmup,
+            # one entry of each correlator: sink slice y0 in Gamma*_0, source slice x0 in Gamma-bar_0
+            "pion_C_y40_x4": [float(Cpi[40, 4].real), float(Cpi[40, 4].imag)],
+            "nucleon_C_y40_x4": [float(Cn[40, 4].real), float(Cn[40, 4].imag)]}
+
+
 # ----------------------------------------------------------------------- serving
 
 SERVE_CLASSES = [((4, 4, 4, 4), 0.1555), ((8, 8, 8, 8), 0.1555), ((4, 32, 32, 32), 0.1555),
