@@ -73,7 +73,7 @@ def hop_traffic_record():
     try:
         rec = json.load(open(p))
         h = hashlib.sha256()
-        for f in ("ddp_device.cuh", "ddp_kernels.cuh"):
+        for f in ("ddp_device.cuh", "ddp_kernels.cuh", "clover.cuh"):
             h.update(open(os.path.join(ROOT, "paper_1601_04587_gb300", "csrc", f), "rb").read())
         if rec.get("sources_sha256") != h.hexdigest():
             return None
