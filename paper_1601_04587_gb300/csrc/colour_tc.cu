@@ -1,0 +1,574 @@
+// Time-slice sums of the colourless spinors (Sec. 5, Eq. W0tbary) on the tensor
+// cores with FP64-level accuracy.
+//
+// Per time slice the sum is a complex matrix product
+//   X[(i,j)][(k,alpha)] = sum_{(x,c)} E[(i,j)][(x,c)] s_k(x)_{alpha c},
+//   E[(i,j)][(x,c)] = sum_{ab} eps_abc (s_i^a)^T C g5 s_j^b          (the diquark, FP64).
+// C g5 is antisymmetric, so E is symmetric in (i, j): only the m(m+1)/2 rows i <= j
+// are formed and X[j][i] = X[i][j].  The complex product is one real product
+// C' = A' B'^T with A' = [Re E | Im E] and the rows of B' = [Re s | -Im s] (real-part
+// columns) and [Im s | Re s] (imaginary-part columns).
+//
+// Every row of A' and every column of B' is split into S integer slices of 7 bits
+// under a shared power-of-two exponent (the error-free splitting of Ozaki, Ogita,
+// Oishi and Rump, 2012):  a = 2^(e-7) sum_p q_p 2^(-7p), q_0 in [-128, 128],
+// q_p in [-64, 64] for p > 0, exact in BF16.  For every d < S the products of slices
+// p + q = d are summed on the tensor cores (tcgen05.mma kind::f16, BF16 operands,
+// FP32 accumulators in tensor memory, one per d).  Over KC = 256 reduction terms
+// every such sum is an integer of magnitude below 9 * 2^12 * 256 < 2^24, hence
+// exact in FP32; after each chunk the seven sums are converted to integers and
+// added exactly into two 64-bit fixed-point accumulators per output.  Products of
+// slices with p + q >= S are dropped: each term of the sum is exact to about
+// 2^-47 of its row maximum times its column maximum.
+//
+// Operands reach the tensor cores through a two-stage pipeline of bulk copies
+// (cp.async.bulk, completion on an mbarrier): the split kernels write every
+// (slice, 128- or 64-row tile, 32-deep K step) block contiguously in the
+// shared-memory layout the MMA descriptor describes (K-major, no swizzle: 8-row x
+// 16-byte core matrices, 128 bytes apart along K, 512 bytes apart between 8-row
+// groups), so that one copy per block stages it.
+#include <cmath>
+#include <cstring>
+
+#include "ddp_host.h"
+
+using namespace ddp;
+
+namespace {
+
+constexpr int S = 7;          // slices per operand; accumulator groups d = p + q < S
+constexpr int TM = 128;       // rows of A' per tile (the MMA's M)
+constexpr int TN = 64;        // rows of B' (output columns) per tile (the MMA's N)
+constexpr int KSTEP = 32;     // reduction depth per pipeline stage (two MMAs of K = 16)
+constexpr int CS = 8;         // stages per exact chunk: KC = 256
+constexpr int SBO = 512, LBO = 128;
+constexpr int TILE_A = TM * KSTEP * 2, TILE_B = TN * KSTEP * 2;  // bytes
+constexpr int STAGE = S * (TILE_A + TILE_B);
+constexpr int NSTAGE = 2;
+constexpr int GEMM_THREADS = 512;
+constexpr int DCOLS = TN / (GEMM_THREADS / 128);  // accumulator columns a thread drains
+constexpr int TMEM_COLS = 512;  // S * TN = 448 used
+constexpr int MAX_STEPS_PER_BLOCK = 1 << 16;  // keeps the fixed-point sums far below 2^63
+constexpr int ESITES = 16;    // sites per block of the diquark kernel
+constexpr int MMAX = 32;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
+
+static_assert(S * TN <= TMEM_COLS, "accumulators exceed the tensor memory");
+static_assert(DCOLS == 16, "the drain loads 16 columns per thread");
+static_assert(CS * KSTEP * 9 * 4096 < (1 << 24), "chunk sums must stay exact in FP32");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t mma_desc(uint32_t saddr) {
+    return ((uint64_t)(saddr >> 4) & 0x3FFF) | ((uint64_t)((LBO >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the completion of the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0;; it++) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred pw;\n mbarrier.try_wait.parity.shared::cta.b64 pw, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, pw;\n}\n"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 255u && globaltimer() - t0 > WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ double2 cm(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+__device__ __forceinline__ void atomic_max_pos(double *a, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long *>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ int exponent_of(double mx) {
+    if (!(mx > 0)) return 0;
+    int e;
+    frexp(mx, &e);  // mx < 2^e
+    return e;
+}
+
+// (i, j), i <= j, of the symmetric row r (rows ordered i-major).
+__device__ __forceinline__ void pair_of(int r, int m, int &i, int &j) {
+    i = 0;
+    while (r >= m - i) {
+        r -= m - i;
+        i++;
+    }
+    j = i + r;
+}
+
+// spinor component of the source field in the requested form: 0 s = A,
+// 1 s = g5 conj(A), 2 s = -A (g5 = diag(-1, -1, 1, 1) in the chiral basis)
+__device__ __forceinline__ double2 form_of(double2 v, int form, int spin) {
+    if (form == 1) {
+        v.y = -v.y;
+        if (spin < 2) v = make_double2(-v.x, -v.y);
+    } else if (form == 2) {
+        v = make_double2(-v.x, -v.y);
+    }
+    return v;
+}
+
+// ------------------------------------------------------------- pre-passes
+
+struct EArgs {
+    const double2 *A;   // [m][n][12]
+    int64_t n, site0, slice_n;
+    int m, form, rows;  // rows = m (m + 1) / 2
+    double2 *E;         // [rows][3 slice_n]
+    double *rowmax;     // [rows]   max |Re|, |Im| of the row of E
+    double *colmax;     // [4 m]    max |Re|, |Im| of s_k(x)_{alpha c} over x, c
+};
+
+// The diquarks E^c_ij(x) = i sum over the spin pairs of Eq. W0tbary for i <= j, with the
+// row and column maxima.  Block: ESITES sites, all rows; 16 consecutive threads share a row.
+__global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
+    extern __shared__ double2 sh[];  // [m][ESITES][12]
+    const int m = a.m;
+    const int64_t x0 = (int64_t)blockIdx.x * ESITES;
+    const int ns = (int)min((int64_t)ESITES, a.slice_n - x0);
+    for (int e = threadIdx.x; e < m * ns * 12; e += blockDim.x) {
+        const int c = e % 12, xs = (e / 12) % ns, k = e / (12 * ns);
+        const double2 v = a.A[((int64_t)k * a.n + a.site0 + x0 + xs) * 12 + c];
+        sh[(k * ESITES + xs) * 12 + c] = form_of(v, a.form, c / 3);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 4 * m; q += blockDim.x) {
+        const int k = q / 4, al = q % 4;
+        double mx = 0;
+        for (int xs = 0; xs < ns; xs++)
+            for (int c = 0; c < 3; c++) {
+                const double2 v = sh[(k * ESITES + xs) * 12 + 3 * al + c];
+                mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+            }
+        if (mx > 0) atomic_max_pos(a.colmax + q, mx);
+    }
+    const int nit = a.rows * ESITES;
+    for (int it0 = 0; it0 < nit; it0 += blockDim.x) {
+        const int it = it0 + threadIdx.x;
+        const int r = it / ESITES, xs = it % ESITES;
+        double mx = 0;
+        if (r < a.rows && xs < ns) {
+            int i, j;
+            pair_of(r, m, i, j);
+            const double2 *si = sh + (i * ESITES + xs) * 12, *sj = sh + (j * ESITES + xs) * 12;
+            double2 *o = a.E + (int64_t)r * 3 * a.slice_n + (x0 + xs) * 3;
+            for (int c = 0; c < 3; c++) {
+                const int ca = (c + 1) % 3, cb = (c + 2) % 3;
+                // f(a, b) = s_i(1,a) s_j(0,b) - s_i(0,a) s_j(1,b) + s_i(3,a) s_j(2,b) - s_i(2,a) s_j(3,b);
+                // E^c = i [f(ca, cb) - f(cb, ca)]
+                double re = 0, im = 0;
+                for (int t = 0; t < 2; t++) {
+                    const double sg = t ? -1.0 : 1.0;
+                    const int p = t ? cb : ca, q = t ? ca : cb;
+                    const double2 t1 = cm(si[3 + p], sj[q]), t2 = cm(si[p], sj[3 + q]);
+                    const double2 t3 = cm(si[9 + p], sj[6 + q]), t4 = cm(si[6 + p], sj[9 + q]);
+                    re += sg * (t1.x - t2.x + t3.x - t4.x);
+                    im += sg * (t1.y - t2.y + t3.y - t4.y);
+                }
+                o[c] = make_double2(-im, re);
+                mx = fmax(mx, fmax(fabs(re), fabs(im)));
+            }
+        }
+        for (int off = 8; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if ((threadIdx.x & 15) == 0 && r < a.rows && mx > 0) atomic_max_pos(a.rowmax + r, mx);
+    }
+}
+
+// The S 7-bit integer slices of v / 2^e (|v| < 2^e), in BF16.
+__device__ __forceinline__ void split7(double v, int e, __nv_bfloat16 out[S]) {
+    double t = ldexp(v, -e);
+#pragma unroll
+    for (int p = 0; p < S; p++) {
+        t *= 128.0;
+        const double q = rint(t);
+        out[p] = __double2bfloat16(q);  // |q| <= 128: exact
+        t -= q;
+    }
+}
+
+// (row rl, depth kl) of element e of one tile block in the MMA's shared-memory layout.
+__device__ __forceinline__ void tile_pos(int e, int &rl, int &kl) {
+    rl = ((e >> 3) & 7) + 8 * (e >> 8);
+    kl = (e & 7) + 8 * ((e >> 6) & 3);
+}
+
+struct SplitArgs {
+    const double2 *E;
+    const double2 *A;
+    int64_t n, site0, K;  // K = 3 slice_n
+    int m, form, rows;
+    int MT, NT, KSh;      // tiles; K steps of one half (Re / Im) of the reduction
+    const double *rowmax, *colmax;
+    __nv_bfloat16 *Aq, *Bq;  // [S][MT][2 KSh][128 x 32], [S][NT][2 KSh][64 x 32]
+};
+
+// A' = [Re E | Im E]: thread per (row, kx), writes the slices of both halves.
+__global__ void k_split_A(SplitArgs a) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)a.MT * a.KSh * (TM * KSTEP);
+    if (g >= total) return;
+    const int e = (int)(g % (TM * KSTEP));
+    const int64_t t = g / (TM * KSTEP);
+    const int ksr = (int)(t % a.KSh), mt = (int)(t / a.KSh);
+    int rl, kl;
+    tile_pos(e, rl, kl);
+    const int r = mt * TM + rl;
+    const int64_t kx = (int64_t)ksr * KSTEP + kl;
+    __nv_bfloat16 re[S], im[S];
+    if (r < a.rows && kx < a.K) {
+        const double2 v = a.E[(int64_t)r * a.K + kx];
+        const int ex = exponent_of(a.rowmax[r]);
+        split7(v.x, ex, re);
+        split7(v.y, ex, im);
+    } else {
+        for (int p = 0; p < S; p++) re[p] = im[p] = __double2bfloat16(0.0);
+    }
+    const int KS = 2 * a.KSh;
+    for (int p = 0; p < S; p++) {
+        const int64_t base = ((int64_t)p * a.MT + mt) * KS;
+        a.Aq[(base + ksr) * (TM * KSTEP) + e] = re[p];
+        a.Aq[(base + a.KSh + ksr) * (TM * KSTEP) + e] = im[p];
+    }
+}
+
+// B' rows: col < 4m: [Re s | -Im s]; 4m <= col < 8m: [Im s | Re s]; beyond: zero.
+__global__ void k_split_B(SplitArgs a) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)a.NT * a.KSh * (TN * KSTEP);
+    if (g >= total) return;
+    const int e = (int)(g % (TN * KSTEP));
+    const int64_t t = g / (TN * KSTEP);
+    const int ksr = (int)(t % a.KSh), nt = (int)(t / a.KSh);
+    int rl, kl;
+    tile_pos(e, rl, kl);
+    const int col = nt * TN + rl;
+    const int64_t kx = (int64_t)ksr * KSTEP + kl;
+    const int Q = 4 * a.m;
+    __nv_bfloat16 lo[S], hi[S];
+    if (col < 2 * Q && kx < a.K) {
+        const int q = col < Q ? col : col - Q;
+        const int k = q / 4, al = q % 4;
+        const int64_t x = kx / 3;
+        const int c = (int)(kx % 3);
+        const double2 v = form_of(a.A[((int64_t)k * a.n + a.site0 + x) * 12 + 3 * al + c], a.form, al);
+        const int ex = exponent_of(a.colmax[q]);
+        split7(col < Q ? v.x : v.y, ex, lo);
+        split7(col < Q ? -v.y : v.x, ex, hi);
+    } else {
+        for (int p = 0; p < S; p++) lo[p] = hi[p] = __double2bfloat16(0.0);
+    }
+    const int KS = 2 * a.KSh;
+    for (int p = 0; p < S; p++) {
+        const int64_t base = ((int64_t)p * a.NT + nt) * KS;
+        a.Bq[(base + ksr) * (TN * KSTEP) + e] = lo[p];
+        a.Bq[(base + a.KSh + ksr) * (TN * KSTEP) + e] = hi[p];
+    }
+}
+
+// -------------------------------------------------------------- the product
+
+struct GemmArgs {
+    const uint8_t *Aq, *Bq;
+    int MT, NT, KS, ksplit;
+    int ncols;        // NT * TN
+    double *part;     // [ksplit][MT * TM][ncols]: sum_d 2^-7d G_d of this block's K range
+    int *err;         // set when a wait gave up
+};
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// One CTA per (128-row tile, 64-column tile, K range).  Thread 0 streams the operand
+// blocks and issues the MMAs; after every CS stages all sixteen warps drain the seven
+// accumulators (warp w: lanes 32 (w % 4) .. + 31, columns DCOLS (w / 4) .. + DCOLS - 1).
+__global__ void __launch_bounds__(GEMM_THREADS, 1) k_ozaki_gemm(GemmArgs a) {
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE];
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mt = blockIdx.x, nt = blockIdx.y, z = blockIdx.z;
+    const int s0 = (int)((int64_t)a.KS * z / a.ksplit), s1 = (int)((int64_t)a.KS * (z + 1) / a.ksplit);
+    const int nsteps = s1 - s0;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                     "n"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tbase;
+
+    auto load = [&](int j) {  // thread 0: K step s0 + j into buffer j % 2
+        const int st = j & 1;
+        const uint32_t sa = smem_u32(dsm + st * STAGE), sb = sa + S * TILE_A;
+        const uint32_t fb = smem_u32(&full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"((uint32_t)STAGE)
+                     : "memory");
+        for (int p = 0; p < S; p++) {
+            bulk_copy(sa + p * TILE_A, a.Aq + (((int64_t)p * a.MT + mt) * a.KS + s0 + j) * TILE_A, TILE_A, fb);
+            bulk_copy(sb + p * TILE_B, a.Bq + (((int64_t)p * a.NT + nt) * a.KS + s0 + j) * TILE_B, TILE_B, fb);
+        }
+    };
+
+    int64_t acc_hi[DCOLS], acc_lo[DCOLS];  // 2^14 sum_{d<=2} 2^-7d G_d and 2^42 sum_{d>=3} 2^-7d G_d
+#pragma unroll
+    for (int c = 0; c < DCOLS; c++) acc_hi[c] = acc_lo[c] = 0;
+    int pend_load = -1, pend_mma = -1;  // thread 0: a copy or MMAs not yet waited for
+    bool ok = true, aborted = false;
+    if (tid == 0 && nsteps > 0) {
+        load(0);
+        pend_load = 0;
+    }
+    for (int j = 0; j < nsteps; j++) {
+        const int st = j & 1;
+        if (tid == 0 && ok) {
+            ok = mbar_wait(smem_u32(&full[st]), (j >> 1) & 1);
+            if (ok) {
+                pend_load = -1;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = smem_u32(dsm + st * STAGE), sb = sa + S * TILE_A;
+                for (int p = 0; p < S; p++)
+                    for (int q = 0; p + q < S; q++) {
+                        const uint32_t dcol = tmem + (uint32_t)((p + q) * TN);
+#pragma unroll
+                        for (int kk = 0; kk < KSTEP / 16; kk++) {
+                            const uint64_t da = mma_desc(sa + p * TILE_A + kk * 2 * LBO);
+                            const uint64_t db = mma_desc(sb + q * TILE_B + kk * 2 * LBO);
+                            // the first product of each group in a chunk overwrites the accumulator
+                            const uint32_t accum = (j % CS == 0 && p == 0 && kk == 0) ? 0u : 1u;
+                            asm volatile("{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
+                                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n"
+                                         ::"r"(dcol), "l"(da), "l"(db), "r"(IDESC), "r"(accum)
+                                         : "memory");
+                        }
+                    }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(&empty[st]))
+                             : "memory");
+                pend_mma = j;
+                if (j + 1 < nsteps) {
+                    // the other buffer is free once the MMAs of step j - 1 have read it
+                    if (j >= 1) ok = mbar_wait(smem_u32(&empty[st ^ 1]), ((j - 1) >> 1) & 1);
+                    if (ok) {
+                        load(j + 1);
+                        pend_load = j + 1;
+                    }
+                }
+            }
+            if (!ok) atomicExch(a.err, 1);
+        }
+        if (j % CS == CS - 1 || j == nsteps - 1) {
+            // every thread takes the same branch: the barrier returns the OR of the failures
+            if (__syncthreads_or(tid == 0 && !ok)) {
+                aborted = true;
+                break;
+            }
+            const bool done = mbar_wait(smem_u32(&empty[st]), (j >> 1) & 1);
+            if (!done) atomicExch(a.err, 1);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (done) {
+                const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+                const int cbase = DCOLS * (warp >> 2);
+#pragma unroll
+                for (int d = 0; d < S; d++) {
+                    uint32_t r[DCOLS];
+                    const uint32_t taddr = tmem + lane_base + (uint32_t)(d * TN + cbase);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+                        " [%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(taddr)
+                        : "memory");
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    // G_d is an integer below 2^24: the conversion is exact
+                    const int sh = d <= 2 ? 14 - 7 * d : 42 - 7 * d;
+#pragma unroll
+                    for (int c = 0; c < DCOLS; c++) {
+                        const int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[c])) * (int64_t)(1ll << sh);
+                        if (d <= 2)
+                            acc_hi[c] += v;
+                        else
+                            acc_lo[c] += v;
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (__syncthreads_or(!done)) {
+                aborted = true;
+                break;
+            }
+        }
+    }
+    if (tid == 0) {
+        // after a failed wait: give the copies and MMAs in flight a bounded time to land
+        if (pend_mma >= 0) mbar_wait(smem_u32(&empty[pend_mma & 1]), (pend_mma >> 1) & 1);
+        if (pend_load >= 0) mbar_wait(smem_u32(&full[pend_load & 1]), (pend_load >> 1) & 1);
+    }
+    __syncthreads();
+    if (!aborted) {
+        const int row = mt * TM + 32 * (warp & 3) + lane;
+        double *o = a.part + ((int64_t)z * a.MT * TM + row) * a.ncols + nt * TN + DCOLS * (warp >> 2);
+#pragma unroll
+        for (int c = 0; c < DCOLS; c++) o[c] = ldexp((double)acc_hi[c], -14) + ldexp((double)acc_lo[c], -42);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS) : "memory");
+}
+
+// X[i][j][k][alpha] = X[j][i][k][alpha] = 2^(e_row + e_col - 14) sum over the K-range
+// partials (fixed order).
+__global__ void k_ozaki_finish(const double *part, int ksplit, int prow, int ncols, int m, int rows,
+                               const double *rowmax, const double *colmax, double2 *X) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int Q = 4 * m;
+    if (g >= (int64_t)rows * Q) return;
+    const int r = (int)(g / Q), q = (int)(g % Q);
+    double re = 0, im = 0;
+    for (int s = 0; s < ksplit; s++) {
+        const double *p = part + ((int64_t)s * prow + r) * ncols;
+        re += p[q];
+        im += p[Q + q];
+    }
+    const int sc = exponent_of(rowmax[r]) + exponent_of(colmax[q]) - 14;
+    const double2 v = make_double2(ldexp(re, sc), ldexp(im, sc));
+    int i, j;
+    pair_of(r, m, i, j);
+    X[((int64_t)i * m + j) * Q + q] = v;
+    if (i != j) X[((int64_t)j * m + i) * Q + q] = v;
+}
+
+}  // namespace
+
+namespace ddp {
+
+// Colourless-spinor slice sums of a domain on the tensor cores (fields and forms as
+// ddp_colourless_slices).  A: [m][n][12] on the device; X: L0 x m^3 x 4 complex on the
+// device, slices outside the domain left untouched.
+int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, int64_t slice_n, int nslice, int o0,
+                  int L0, double2 *X) {
+    if (m < 1 || m > MMAX) return DDP_ERR_UNSUPPORTED;
+    const int rows = m * (m + 1) / 2, Q = 4 * m;
+    const int MT = (rows + TM - 1) / TM;
+    const int NT = (2 * Q + TN - 1) / TN;
+    const int64_t K = 3 * slice_n;
+    const int64_t KSh64 = (K + KSTEP - 1) / KSTEP;
+    if (KSh64 > (1 << 28)) return DDP_ERR_UNSUPPORTED;
+    const int KSh = (int)KSh64, KS = 2 * KSh;
+    int ksplit = std::max(1, std::min(KS, 152 / (MT * NT)));
+    ksplit = std::max(ksplit, (KS + MAX_STEPS_PER_BLOCK - 1) / MAX_STEPS_PER_BLOCK);
+    const int ncols = NT * TN, prow = MT * TM;
+    const size_t bE = (size_t)rows * K * sizeof(double2);
+    const size_t bA = (size_t)S * MT * KS * TILE_A, bB = (size_t)S * NT * KS * TILE_B;
+    const size_t bP = (size_t)ksplit * prow * ncols * sizeof(double);
+    Arena &ar = ctx->aux;
+    ar.reset();
+    DDP_CUDA(ctx, ar.reserve(bE + bA + bB + bP + (size_t)(rows + Q) * 8 + 64 + 8 * 256));
+    double2 *E = (double2 *)ar.take(bE);
+    uint8_t *Aq = (uint8_t *)ar.take(bA);
+    uint8_t *Bq = (uint8_t *)ar.take(bB);
+    double *part = (double *)ar.take(bP);
+    double *rowmax = (double *)ar.take((size_t)rows * 8);
+    double *colmax = (double *)ar.take((size_t)Q * 8);
+    int *err = (int *)ar.take(64);
+    const size_t esm = (size_t)m * ESITES * 12 * sizeof(double2);
+    const size_t gsm = (size_t)NSTAGE * STAGE;
+    DDP_CUDA(ctx, cudaFuncSetAttribute(k_colour_E, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+    DDP_CUDA(ctx, cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    cudaStream_t st = ctx->stream;
+    DDP_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
+    for (int z = 0; z < nslice; z++) {
+        const int64_t site0 = (int64_t)z * slice_n;
+        DDP_CUDA(ctx, cudaMemsetAsync(rowmax, 0, (size_t)rows * 8, st));
+        DDP_CUDA(ctx, cudaMemsetAsync(colmax, 0, (size_t)Q * 8, st));
+        EArgs ea;
+        ea.A = A;
+        ea.n = n;
+        ea.site0 = site0;
+        ea.slice_n = slice_n;
+        ea.m = m;
+        ea.form = form;
+        ea.rows = rows;
+        ea.E = E;
+        ea.rowmax = rowmax;
+        ea.colmax = colmax;
+        k_colour_E<<<(unsigned)((slice_n + ESITES - 1) / ESITES), 256, esm, st>>>(ea);
+        SplitArgs sa;
+        sa.E = E;
+        sa.A = A;
+        sa.n = n;
+        sa.site0 = site0;
+        sa.K = K;
+        sa.m = m;
+        sa.form = form;
+        sa.rows = rows;
+        sa.MT = MT;
+        sa.NT = NT;
+        sa.KSh = KSh;
+        sa.rowmax = rowmax;
+        sa.colmax = colmax;
+        sa.Aq = (__nv_bfloat16 *)Aq;
+        sa.Bq = (__nv_bfloat16 *)Bq;
+        const int64_t na = (int64_t)MT * KSh * TM * KSTEP, nb = (int64_t)NT * KSh * TN * KSTEP;
+        k_split_A<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(sa);
+        k_split_B<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(sa);
+        GemmArgs g;
+        g.Aq = Aq;
+        g.Bq = Bq;
+        g.MT = MT;
+        g.NT = NT;
+        g.KS = KS;
+        g.ksplit = ksplit;
+        g.ncols = ncols;
+        g.part = part;
+        g.err = err;
+        k_ozaki_gemm<<<dim3(MT, NT, ksplit), GEMM_THREADS, gsm, st>>>(g);
+        const int64_t nx = (int64_t)rows * Q;
+        k_ozaki_finish<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(
+            part, ksplit, prow, ncols, m, rows, rowmax, colmax, X + (int64_t)((o0 + z) % L0) * m * m * Q);
+        ctx->launches += 5;
+        DDP_CUDA(ctx, cudaGetLastError());
+    }
+    int h = 0;
+    DDP_CUDA(ctx, cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DDP_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h) {
+        snprintf(ctx->last_error, sizeof(ctx->last_error), "colourless spinors: a wait for the tensor cores gave up");
+        return DDP_ERR_CUDA;
+    }
+    return DDP_OK;
+}
+
+}  // namespace ddp

@@ -80,6 +80,7 @@ struct EngineParams {
     int CG_prec[4] = {0, 0, 0, 0};  // columns per block chosen by ddp_autotune, per storage format
     int use_conditional = 1;    // device-driven while loop in a CUDA graph
     int host_chunk = 16;        // iterations per host check without conditional nodes
+    int colour_tc = 1;          // colourless-spinor sums on the tensor cores (0: direct FP64 kernel)
 };
 
 // A growable device arena owned by the context.
@@ -148,6 +149,9 @@ int set_cuda_error(ddp_ctx *ctx, cudaError_t e, const char *where);
 // (least recently used first out, CLOVER_CACHE pairs).
 constexpr int CLOVER_CACHE = 4;
 int clover_for(ddp_ctx *ctx, GaugeDev &g, double kappa, double csw, const CloverDev **out);
+// Colourless-spinor time-slice sums on the tensor cores (device fields; X zeroed by the caller).
+int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, int64_t slice_n, int nslice, int o0,
+                  int L0, double2 *X);
 
 #define DDP_CUDA(ctx, call)                                          \
     do {                                                            \

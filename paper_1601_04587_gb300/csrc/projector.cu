@@ -639,6 +639,13 @@ int ddp_colourless_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, i
     DevBuf ba, bo;
     if ((rc = ba.init(ctx, A, (size_t)m * d->n * 12 * sizeof(double2), true))) return rc;
     if ((rc = bo.init(ctx, X_out, (size_t)L0 * per * sizeof(double2), false))) return rc;
+    DDP_CUDA(ctx, cudaMemsetAsync(bo.dev, 0, (size_t)L0 * per * sizeof(double2), ctx->stream));
+    if (ctx->prm.colour_tc) {
+        rc = colourless_tc(ctx, (const double2 *)ba.dev, d->n, m, form, slice_n, d->e[0], d->o[0], L0,
+                           (double2 *)bo.dev);
+        if (rc) return rc;
+        return bo.copy_out();
+    }
     BaryArgs a;
     a.A = (const double2 *)ba.dev;
     a.n = d->n;
@@ -655,7 +662,6 @@ int ddp_colourless_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, i
     ar.reset();
     DDP_CUDA(ctx, ar.reserve(pb + 1024));
     a.part = (double2 *)ar.take(pb);
-    DDP_CUDA(ctx, cudaMemsetAsync(bo.dev, 0, (size_t)L0 * per * sizeof(double2), ctx->stream));
     dim3 grid(m, a.nchunk, a.nslice);
     k_colourless<<<grid, 256, 0, ctx->stream>>>(a);
     const int64_t n = (int64_t)a.nslice * per;

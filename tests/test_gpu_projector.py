@@ -95,17 +95,118 @@ def test_gram_slices_matches_oracle(ddp, env):
     ddp.ddp_free_domain(ctx, did)
 
 
+# Tensor-core path: every term of a slice sum is exact to ~2^-47 of its row maximum
+# times its column maximum (seven 7-bit slices per operand, exact integer
+# accumulation), so on random fields the norm-wise error stays near 1e-14; the
+# bound 1e-12 leaves the factor ~40 of max/rms of the two operands.  The direct
+# FP64 kernel rounds only in FP64.
+TC_TOL = 1e-12
+
+
+def _forms(A, form):
+    g5 = oracle.gamma()[4]
+    return {0: A, 1: np.einsum("ab,mnbc->mnac", g5, np.conj(A)), 2: -A}[form]
+
+
+@pytest.mark.parametrize("tc", [1, 0])
 @pytest.mark.parametrize("form", [0, 1, 2])
-def test_colourless_slices_matches_oracle(ddp, env, form):
+def test_colourless_slices_matches_oracle(ddp, env, form, tc):
     U, ctx, doms = env
     n = oracle.box_sites(GSTAR[1])
     A = synth.random_spinor(5, n, 13)
     X = torch.zeros((L[0], 5, 5, 5, 4), dtype=torch.complex128, device="cuda")
-    ddp.ddp_colourless_slices(ctx, doms["star"], _dev(A), 5, form, X)
-    g5 = oracle.gamma()[4]
-    s = {0: A, 1: np.einsum("ab,mnbc->mnac", g5, np.conj(A)), 2: -A}[form]
-    want = projector.colourless_spinors(L, *GSTAR, s)
-    assert _rel(X.cpu().numpy(), want) < 1e-12
+    ddp.ddp_set_param(ctx, "colour_tensor_cores", tc)
+    try:
+        ddp.ddp_colourless_slices(ctx, doms["star"], _dev(A), 5, form, X)
+    finally:
+        ddp.ddp_set_param(ctx, "colour_tensor_cores", 1)
+    want = projector.colourless_spinors(L, *GSTAR, _forms(A, form))
+    assert _rel(X.cpu().numpy(), want) < (TC_TOL if tc else 1e-13)
+
+
+# A lattice whose time slices hold 512 sites: with m = 20 and m = 32 the tensor-core
+# product spans several 128-row and 64-column tiles with ragged tails, and (m = 32)
+# more than one exact 256-deep chunk per thread block.
+L8 = (6, 8, 8, 8)
+
+
+@pytest.fixture(scope="module")
+def env8(ddp):
+    U = synth.gauge_field(L8, seed=43)
+    ctx = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    gid = ddp.ddp_load_gauge(ctx, torch.from_numpy(U).cuda(), L8, ddp.DDP_BC_PERIODIC)
+    yield ctx, gid
+    ddp.ddp_destroy(ctx)
+
+
+def _colourless_both(ddp, ctx, did, A, m, form, L0):
+    out = []
+    for tc in (1, 0):
+        X = torch.zeros((L0, m, m, m, 4), dtype=torch.complex128, device="cuda")
+        ddp.ddp_set_param(ctx, "colour_tensor_cores", tc)
+        try:
+            ddp.ddp_colourless_slices(ctx, did, _dev(A), m, form, X)
+        finally:
+            ddp.ddp_set_param(ctx, "colour_tensor_cores", 1)
+        out.append(X.cpu().numpy())
+    return out
+
+
+@pytest.mark.parametrize("m,form,box", [(20, 1, ((1, 0, 0, 0), (3, 8, 8, 8))),
+                                        (32, 0, ((4, 0, 0, 0), (2, 8, 8, 8))),
+                                        (1, 2, ((5, 0, 0, 0), (3, 8, 8, 8)))])
+def test_colourless_tensor_cores_several_tiles(ddp, env8, m, form, box):
+    ctx, gid = env8
+    did = ddp.ddp_set_domain(ctx, gid, *box)
+    A = synth.random_spinor(m, oracle.box_sites(box[1]), 50 + m)
+    tc, direct = _colourless_both(ddp, ctx, did, A, m, form, L8[0])
+    want = projector.colourless_spinors(L8, *box, _forms(A, form))
+    ddp.ddp_free_domain(ctx, did)
+    assert _rel(direct, want) < 1e-13
+    assert _rel(tc, want) < TC_TOL
+    # the slices outside the domain stay zero (the box wraps in time for the last case)
+    inside = np.zeros(L8[0], bool)
+    inside[[(box[0][0] + t) % L8[0] for t in range(box[1][0])]] = True
+    assert not np.any(tc[~inside])
+
+
+def test_colourless_tensor_cores_wide_dynamic_range(ddp, env8):
+    """Columns scaled over 12 decades: every (i, j, k) block keeps its relative accuracy,
+    because each row of the diquark matrix and each spinor column carries its own exponent."""
+    ctx, gid = env8
+    box = ((0, 0, 0, 0), (2, 8, 8, 8))
+    did = ddp.ddp_set_domain(ctx, gid, *box)
+    m = 6
+    A = synth.random_spinor(m, oracle.box_sites(box[1]), 77) * (10.0 ** np.linspace(-6, 6, m))[:, None, None, None]
+    tc, _ = _colourless_both(ddp, ctx, did, A, m, 0, L8[0])
+    want = projector.colourless_spinors(L8, *box, A)
+    ddp.ddp_free_domain(ctx, did)
+    for t in range(2):
+        for i in range(m):
+            for j in range(m):
+                for k in range(m):
+                    w = want[t, i, j, k]
+                    assert np.linalg.norm(tc[t, i, j, k] - w) <= TC_TOL * np.linalg.norm(w) + 1e-300
+
+
+def test_colourless_tensor_cores_full_slice(ddp):
+    """One 24^3 time slice with 24 columns, the size of every slice of the projector
+    workload: the tensor-core sums against the oracle and the direct FP64 kernel."""
+    L24 = (2, 24, 24, 24)
+    box = ((0, 0, 0, 0), (1, 24, 24, 24))
+    m = 24
+    ctx = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        U = synth.gauge_field(L24, seed=44)
+        gid = ddp.ddp_load_gauge(ctx, torch.from_numpy(U).cuda(), L24, ddp.DDP_BC_PERIODIC)
+        did = ddp.ddp_set_domain(ctx, gid, *box)
+        A = synth.random_spinor(m, oracle.box_sites(box[1]), 91)
+        tc, direct = _colourless_both(ddp, ctx, did, A, m, 1, L24[0])
+    finally:
+        ddp.ddp_destroy(ctx)
+    want = projector.colourless_spinors(L24, *box, _forms(A, 1))
+    assert _rel(direct, want) < 1e-13
+    assert _rel(tc, want) < TC_TOL
 
 
 def test_colourless_slices_rejects_too_many_columns(ddp, env):
