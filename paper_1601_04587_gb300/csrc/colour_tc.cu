@@ -10,9 +10,10 @@
 // columns) and [Im s | Re s] (imaginary-part columns).
 //
 // Every row of A' and every column of B' is split into S integer slices of 7 bits
-// under a shared power-of-two exponent (the error-free splitting of Ozaki, Ogita,
-// Oishi and Rump, 2012):  a = 2^(e-7) sum_p q_p 2^(-7p), q_0 in [-128, 128],
-// q_p in [-64, 64] for p > 0, exact in BF16.  For every d < S the products of slices
+// under a shared power-of-two exponent (the splitting of Ozaki, Ogita, Oishi and Rump,
+// 2012): with |a| < 2^e over the row (column), N = round(a 2^(49-e)) is written in
+// balanced base 128, a = 2^(e-7) sum_p q_p 2^(-7p) + O(2^(e-50)), q_0 in [-128, 128],
+// q_p in [-64, 63] for p > 0, each exact in BF16.  For every d < S the products of slices
 // p + q = d are summed on the tensor cores (tcgen05.mma kind::f16, BF16 operands,
 // FP32 accumulators in tensor memory, one per d).  Over KC = 256 reduction terms
 // every such sum is an integer of magnitude below 9 * 2^12 * 256 < 2^24, hence
@@ -88,8 +89,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     }
 }
 
-__device__ __forceinline__ double2 cm(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-
 __device__ __forceinline__ void atomic_max_pos(double *a, double v) {
     // non-negative doubles order like their bit patterns
     atomicMax(reinterpret_cast<unsigned long long *>(a), (unsigned long long)__double_as_longlong(v));
@@ -125,39 +124,105 @@ __device__ __forceinline__ double2 form_of(double2 v, int form, int spin) {
 }
 
 // ------------------------------------------------------------- pre-passes
+//
+// GB300 runs FP64 arithmetic at a small fraction of its FP32 rate, so the pre-passes
+// avoid it: the diquarks are formed in double-FP32 arithmetic (each value an unevaluated
+// sum hi + lo of two floats, 48 significant bits; Dekker's product with fused
+// multiply-adds and Knuth's two-sum), and the 7-bit slices are cut from the integer
+// round(v 2^(49-e)) obtained from the bit pattern of v by shifts.
+
+// Magnitude used for the shared exponents: +inf for a non-finite value, so that a NaN or
+// an infinity in the input turns the affected outputs into NaN (see k_ozaki_finish).
+__device__ __forceinline__ double mag(double v) { return isfinite(v) ? fabs(v) : (double)INFINITY; }
+
+__device__ __forceinline__ float2 df_of(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+// (S, E) += sg * a * b for double-float a, b; (S, E) is an unnormalized sum.
+__device__ __forceinline__ void df_mac(float &S, float &E, float2 a, float2 b, float sg) {
+    const float ah = sg * a.x, al = sg * a.y;
+    const float p = __fmul_rn(ah, b.x);
+    float e = __fmaf_rn(ah, b.x, -p);
+    e = __fmaf_rn(ah, b.y, e);
+    e = __fmaf_rn(al, b.x, e);
+    const float s = __fadd_rn(S, p);
+    const float bb = __fsub_rn(s, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    E = __fadd_rn(E, __fadd_rn(err, e));
+    S = s;
+}
+
+__device__ __forceinline__ float2 df_norm(float S, float E) {
+    const float h = __fadd_rn(S, E);
+    return make_float2(h, __fsub_rn(E, __fsub_rn(h, S)));
+}
+
+// (S_re, E_re, S_im, E_im) += sg * a * b for double-float complex a, b (float4: re h, re l,
+// im h, im l).
+__device__ __forceinline__ void dfc_mac(float acc[4], float4 a, float4 b, float sg) {
+    const float2 ar = make_float2(a.x, a.y), ai = make_float2(a.z, a.w);
+    const float2 br = make_float2(b.x, b.y), bi = make_float2(b.z, b.w);
+    df_mac(acc[0], acc[1], ar, br, sg);
+    df_mac(acc[0], acc[1], ai, bi, -sg);
+    df_mac(acc[2], acc[3], ar, bi, sg);
+    df_mac(acc[2], acc[3], ai, br, sg);
+}
+
+// Column maxima of the spinors over one time slice: colmax[q], q = (k, alpha), the
+// largest |Re|, |Im| of s_k(x)_{alpha c} over x and c.
+__global__ void __launch_bounds__(256) k_colour_max(const double2 *A, int64_t n, int64_t site0, int64_t slice_n,
+                                                    int m, double *colmax) {
+    __shared__ double bm[128];
+    const int Q = 4 * m, per = blockDim.x / Q;
+    for (int q = threadIdx.x; q < Q; q += blockDim.x) bm[q] = 0;
+    __syncthreads();
+    if ((int)threadIdx.x < per * Q) {
+        const int q = threadIdx.x % Q, k = q / 4, al = q % 4;
+        double mx = 0;
+        for (int64_t x = blockIdx.x * (int64_t)per + threadIdx.x / Q; x < slice_n; x += (int64_t)gridDim.x * per)
+            for (int c = 0; c < 3; c++) {
+                const double2 v = A[((int64_t)k * n + site0 + x) * 12 + 3 * al + c];
+                mx = fmax(mx, fmax(mag(v.x), mag(v.y)));
+            }
+        if (mx > 0) atomic_max_pos(bm + q, mx);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < Q; q += blockDim.x)
+        if (bm[q] > 0) atomic_max_pos(colmax + q, bm[q]);
+}
+
+// f_k: |s_k(x)| < 2^f_k over the slice (the exponent of the spinor column k).
+__device__ __forceinline__ int column_exponent(const double *colmax, int k) {
+    return exponent_of(fmax(fmax(colmax[4 * k], colmax[4 * k + 1]), fmax(colmax[4 * k + 2], colmax[4 * k + 3])));
+}
 
 struct EArgs {
     const double2 *A;   // [m][n][12]
     int64_t n, site0, slice_n;
     int m, form, rows;  // rows = m (m + 1) / 2
-    double2 *E;         // [rows][3 slice_n]
-    double *rowmax;     // [rows]   max |Re|, |Im| of the row of E
-    double *colmax;     // [4 m]    max |Re|, |Im| of s_k(x)_{alpha c} over x, c
+    float4 *E;          // [rows][3 slice_n]: Re hi, Re lo, Im hi, Im lo of E 2^-(f_i + f_j)
+    double *rowmax;     // [rows]   max |Re|, |Im| (hi parts) of the row of E 2^-(f_i + f_j)
+    const double *colmax;
 };
 
-// The diquarks E^c_ij(x) = i sum over the spin pairs of Eq. W0tbary for i <= j, with the
-// row and column maxima.  Block: ESITES sites, all rows; 16 consecutive threads share a row.
+// The diquarks E^c_ij(x) = i sum over the spin pairs of Eq. W0tbary for i <= j, formed
+// from the spinors scaled by 2^-f_k (so that double-FP32 arithmetic keeps its range),
+// with the row maxima.  Block: ESITES sites, all rows; 16 consecutive threads share a row.
 __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
-    extern __shared__ double2 sh[];  // [m][ESITES][12]
+    extern __shared__ float4 sh[];  // [m][ESITES][12]
     const int m = a.m;
     const int64_t x0 = (int64_t)blockIdx.x * ESITES;
     const int ns = (int)min((int64_t)ESITES, a.slice_n - x0);
     for (int e = threadIdx.x; e < m * ns * 12; e += blockDim.x) {
         const int c = e % 12, xs = (e / 12) % ns, k = e / (12 * ns);
-        const double2 v = a.A[((int64_t)k * a.n + a.site0 + x0 + xs) * 12 + c];
-        sh[(k * ESITES + xs) * 12 + c] = form_of(v, a.form, c / 3);
+        const double sc = ldexp(1.0, -column_exponent(a.colmax, k));
+        const double2 v = form_of(a.A[((int64_t)k * a.n + a.site0 + x0 + xs) * 12 + c], a.form, c / 3);
+        const float2 re = df_of(v.x * sc), im = df_of(v.y * sc);
+        sh[(k * ESITES + xs) * 12 + c] = make_float4(re.x, re.y, im.x, im.y);
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < 4 * m; q += blockDim.x) {
-        const int k = q / 4, al = q % 4;
-        double mx = 0;
-        for (int xs = 0; xs < ns; xs++)
-            for (int c = 0; c < 3; c++) {
-                const double2 v = sh[(k * ESITES + xs) * 12 + 3 * al + c];
-                mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-            }
-        if (mx > 0) atomic_max_pos(a.colmax + q, mx);
-    }
     const int nit = a.rows * ESITES;
     for (int it0 = 0; it0 < nit; it0 += blockDim.x) {
         const int it = it0 + threadIdx.x;
@@ -166,23 +231,24 @@ __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
         if (r < a.rows && xs < ns) {
             int i, j;
             pair_of(r, m, i, j);
-            const double2 *si = sh + (i * ESITES + xs) * 12, *sj = sh + (j * ESITES + xs) * 12;
-            double2 *o = a.E + (int64_t)r * 3 * a.slice_n + (x0 + xs) * 3;
+            const float4 *si = sh + (i * ESITES + xs) * 12, *sj = sh + (j * ESITES + xs) * 12;
+            float4 *o = a.E + (int64_t)r * 3 * a.slice_n + (x0 + xs) * 3;
             for (int c = 0; c < 3; c++) {
                 const int ca = (c + 1) % 3, cb = (c + 2) % 3;
                 // f(a, b) = s_i(1,a) s_j(0,b) - s_i(0,a) s_j(1,b) + s_i(3,a) s_j(2,b) - s_i(2,a) s_j(3,b);
                 // E^c = i [f(ca, cb) - f(cb, ca)]
-                double re = 0, im = 0;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
                 for (int t = 0; t < 2; t++) {
-                    const double sg = t ? -1.0 : 1.0;
+                    const float sg = t ? -1.f : 1.f;
                     const int p = t ? cb : ca, q = t ? ca : cb;
-                    const double2 t1 = cm(si[3 + p], sj[q]), t2 = cm(si[p], sj[3 + q]);
-                    const double2 t3 = cm(si[9 + p], sj[6 + q]), t4 = cm(si[6 + p], sj[9 + q]);
-                    re += sg * (t1.x - t2.x + t3.x - t4.x);
-                    im += sg * (t1.y - t2.y + t3.y - t4.y);
+                    dfc_mac(acc, si[3 + p], sj[q], sg);
+                    dfc_mac(acc, si[p], sj[3 + q], -sg);
+                    dfc_mac(acc, si[9 + p], sj[6 + q], sg);
+                    dfc_mac(acc, si[6 + p], sj[9 + q], -sg);
                 }
-                o[c] = make_double2(-im, re);
-                mx = fmax(mx, fmax(fabs(re), fabs(im)));
+                const float2 R = df_norm(acc[0], acc[1]), I = df_norm(acc[2], acc[3]);
+                o[c] = make_float4(-I.x, -I.y, R.x, R.y);  // times i
+                mx = fmax(mx, fmax(mag(R.x), mag(I.x)));
             }
         }
         for (int off = 8; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
@@ -190,16 +256,45 @@ __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
     }
 }
 
-// The S 7-bit integer slices of v / 2^e (|v| < 2^e), in BF16.
-__device__ __forceinline__ void split7(double v, int e, __nv_bfloat16 out[S]) {
-    double t = ldexp(v, -e);
+// round(mant 2^(ee + k)), |result| < 2^62 by the caller's choice of k (half away from zero).
+__device__ __forceinline__ long long fixed_round(unsigned long long mant, int sh, bool neg) {
+    unsigned long long n;
+    if (sh >= 0)
+        n = mant << sh;
+    else if (sh > -64)
+        n = (mant + (1ull << (-sh - 1))) >> (-sh);
+    else
+        n = 0;
+    return neg ? -(long long)n : (long long)n;
+}
+
+// round(v 2^k) from the bits of a finite double (subnormals included).
+__device__ __forceinline__ long long fixed_of(double v, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ev = (int)((b >> 52) & 0x7FF);
+    const unsigned long long mant = (b & ((1ull << 52) - 1)) | (ev ? 1ull << 52 : 0ull);
+    return fixed_round(mant, (ev ? ev : 1) - 1075 + k, b >> 63);
+}
+
+// round(f 2^k) from the bits of a finite float.
+__device__ __forceinline__ long long fixed_of(float f, int k) {
+    const unsigned b = __float_as_uint(f);
+    const int ev = (int)((b >> 23) & 0xFF);
+    const unsigned long long mant = (b & 0x7FFFFFu) | (ev ? 0x800000u : 0u);
+    return fixed_round(mant, (ev ? ev : 1) - 150 + k, b >> 31);
+}
+
+// The S balanced base-128 digits of N (|N| <= 2^49 + 1): N = sum_p q_p 128^(S-1-p),
+// q_p in [-64, 63] for p > 0 and |q_0| <= 128; each exact in BF16.
+__device__ __forceinline__ void digits7(long long N, __nv_bfloat16 out[S]) {
 #pragma unroll
-    for (int p = 0; p < S; p++) {
-        t *= 128.0;
-        const double q = rint(t);
-        out[p] = __double2bfloat16(q);  // |q| <= 128: exact
-        t -= q;
+    for (int p = S - 1; p > 0; p--) {
+        int d = (int)(N & 127);
+        if (d >= 64) d -= 128;
+        N = (N - d) >> 7;  // exact: N - d is a multiple of 128
+        out[p] = __int2bfloat16_rn(d);
     }
+    out[0] = __int2bfloat16_rn((int)N);
 }
 
 // (row rl, depth kl) of element e of one tile block in the MMA's shared-memory layout.
@@ -209,7 +304,7 @@ __device__ __forceinline__ void tile_pos(int e, int &rl, int &kl) {
 }
 
 struct SplitArgs {
-    const double2 *E;
+    const float4 *E;
     const double2 *A;
     int64_t n, site0, K;  // K = 3 slice_n
     int m, form, rows;
@@ -218,7 +313,8 @@ struct SplitArgs {
     __nv_bfloat16 *Aq, *Bq;  // [S][MT][2 KSh][128 x 32], [S][NT][2 KSh][64 x 32]
 };
 
-// A' = [Re E | Im E]: thread per (row, kx), writes the slices of both halves.
+// A' = [Re E | Im E]: thread per (row, kx), writes the slices of both halves.  With
+// |v| < 2^e for the row, v = 2^(e-49) round(v 2^(49-e)) to within half a unit.
 __global__ void k_split_A(SplitArgs a) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)a.MT * a.KSh * (TM * KSTEP);
@@ -231,11 +327,11 @@ __global__ void k_split_A(SplitArgs a) {
     const int r = mt * TM + rl;
     const int64_t kx = (int64_t)ksr * KSTEP + kl;
     __nv_bfloat16 re[S], im[S];
-    if (r < a.rows && kx < a.K) {
-        const double2 v = a.E[(int64_t)r * a.K + kx];
-        const int ex = exponent_of(a.rowmax[r]);
-        split7(v.x, ex, re);
-        split7(v.y, ex, im);
+    if (r < a.rows && kx < a.K && isfinite(a.rowmax[r])) {
+        const float4 v = a.E[(int64_t)r * a.K + kx];
+        const int k = 49 - exponent_of(a.rowmax[r]);
+        digits7(fixed_of(v.x, k) + fixed_of(v.y, k), re);
+        digits7(fixed_of(v.z, k) + fixed_of(v.w, k), im);
     } else {
         for (int p = 0; p < S; p++) re[p] = im[p] = __double2bfloat16(0.0);
     }
@@ -260,16 +356,16 @@ __global__ void k_split_B(SplitArgs a) {
     const int col = nt * TN + rl;
     const int64_t kx = (int64_t)ksr * KSTEP + kl;
     const int Q = 4 * a.m;
+    const int q = col < Q ? col : col - Q;
     __nv_bfloat16 lo[S], hi[S];
-    if (col < 2 * Q && kx < a.K) {
-        const int q = col < Q ? col : col - Q;
+    if (col < 2 * Q && kx < a.K && isfinite(a.colmax[q])) {
         const int k = q / 4, al = q % 4;
         const int64_t x = kx / 3;
         const int c = (int)(kx % 3);
         const double2 v = form_of(a.A[((int64_t)k * a.n + a.site0 + x) * 12 + 3 * al + c], a.form, al);
-        const int ex = exponent_of(a.colmax[q]);
-        split7(col < Q ? v.x : v.y, ex, lo);
-        split7(col < Q ? -v.y : v.x, ex, hi);
+        const int sc = 49 - exponent_of(a.colmax[q]);
+        digits7(fixed_of(col < Q ? v.x : v.y, sc), lo);
+        digits7(fixed_of(col < Q ? -v.y : v.x, sc), hi);
     } else {
         for (int p = 0; p < S; p++) lo[p] = hi[p] = __double2bfloat16(0.0);
     }
@@ -462,10 +558,13 @@ __global__ void k_ozaki_finish(const double *part, int ksplit, int prow, int nco
         re += p[q];
         im += p[Q + q];
     }
-    const int sc = exponent_of(rowmax[r]) + exponent_of(colmax[q]) - 14;
-    const double2 v = make_double2(ldexp(re, sc), ldexp(im, sc));
+    // the splits carried v = 2^(e - 49) N = 2^(e - 7) sum_p q_p 2^(-7p) for each operand
     int i, j;
     pair_of(r, m, i, j);
+    const int sc = exponent_of(rowmax[r]) + column_exponent(colmax, i) + column_exponent(colmax, j) +
+                   exponent_of(colmax[q]) - 14;
+    double2 v = make_double2(ldexp(re, sc), ldexp(im, sc));
+    if (!isfinite(rowmax[r]) || !isfinite(colmax[q])) v = make_double2(NAN, NAN);  // a non-finite input
     X[((int64_t)i * m + j) * Q + q] = v;
     if (i != j) X[((int64_t)j * m + i) * Q + q] = v;
 }
@@ -490,20 +589,20 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
     int ksplit = std::max(1, std::min(KS, 152 / (MT * NT)));
     ksplit = std::max(ksplit, (KS + MAX_STEPS_PER_BLOCK - 1) / MAX_STEPS_PER_BLOCK);
     const int ncols = NT * TN, prow = MT * TM;
-    const size_t bE = (size_t)rows * K * sizeof(double2);
+    const size_t bE = (size_t)rows * K * sizeof(float4);
     const size_t bA = (size_t)S * MT * KS * TILE_A, bB = (size_t)S * NT * KS * TILE_B;
     const size_t bP = (size_t)ksplit * prow * ncols * sizeof(double);
     Arena &ar = ctx->aux;
     ar.reset();
     DDP_CUDA(ctx, ar.reserve(bE + bA + bB + bP + (size_t)(rows + Q) * 8 + 64 + 8 * 256));
-    double2 *E = (double2 *)ar.take(bE);
+    float4 *E = (float4 *)ar.take(bE);
     uint8_t *Aq = (uint8_t *)ar.take(bA);
     uint8_t *Bq = (uint8_t *)ar.take(bB);
     double *part = (double *)ar.take(bP);
     double *rowmax = (double *)ar.take((size_t)rows * 8);
     double *colmax = (double *)ar.take((size_t)Q * 8);
     int *err = (int *)ar.take(64);
-    const size_t esm = (size_t)m * ESITES * 12 * sizeof(double2);
+    const size_t esm = (size_t)m * ESITES * 12 * sizeof(float4);
     const size_t gsm = (size_t)NSTAGE * STAGE;
     DDP_CUDA(ctx, cudaFuncSetAttribute(k_colour_E, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
     DDP_CUDA(ctx, cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
@@ -524,6 +623,8 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
         ea.E = E;
         ea.rowmax = rowmax;
         ea.colmax = colmax;
+        k_colour_max<<<(unsigned)std::min<int64_t>(2 * 152, (slice_n + 1) / 2), 256, 0, st>>>(A, n, site0, slice_n,
+                                                                                          m, colmax);
         k_colour_E<<<(unsigned)((slice_n + ESITES - 1) / ESITES), 256, esm, st>>>(ea);
         SplitArgs sa;
         sa.E = E;
@@ -558,7 +659,7 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
         const int64_t nx = (int64_t)rows * Q;
         k_ozaki_finish<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(
             part, ksplit, prow, ncols, m, rows, rowmax, colmax, X + (int64_t)((o0 + z) % L0) * m * m * Q);
-        ctx->launches += 5;
+        ctx->launches += 6;
         DDP_CUDA(ctx, cudaGetLastError());
     }
     int h = 0;

@@ -171,13 +171,15 @@ def test_colourless_tensor_cores_several_tiles(ddp, env8, m, form, box):
 
 
 def test_colourless_tensor_cores_wide_dynamic_range(ddp, env8):
-    """Columns scaled over 12 decades: every (i, j, k) block keeps its relative accuracy,
-    because each row of the diquark matrix and each spinor column carries its own exponent."""
+    """Columns scaled from 1e-30 to 1e6: every (i, j, k) block keeps its relative accuracy,
+    because each spinor column, each row of the diquark matrix and each output column
+    carries its own power-of-two exponent (the diquarks of 1e-30 columns, 1e-60, are far
+    outside the FP32 range that the double-FP32 pre-pass works in)."""
     ctx, gid = env8
     box = ((0, 0, 0, 0), (2, 8, 8, 8))
     did = ddp.ddp_set_domain(ctx, gid, *box)
     m = 6
-    A = synth.random_spinor(m, oracle.box_sites(box[1]), 77) * (10.0 ** np.linspace(-6, 6, m))[:, None, None, None]
+    A = synth.random_spinor(m, oracle.box_sites(box[1]), 77) * (10.0 ** np.linspace(-30, 6, m))[:, None, None, None]
     tc, _ = _colourless_both(ddp, ctx, did, A, m, 0, L8[0])
     want = projector.colourless_spinors(L8, *box, A)
     ddp.ddp_free_domain(ctx, did)
@@ -265,3 +267,35 @@ def test_projected_pion_and_nucleon_pipeline(ddp, env):
     Cn = torch.zeros((L[0], L[0]), dtype=torch.complex128, device="cuda")
     ddp.ddp_projected_nucleon(ctx, L[0], m, X, Y, Cn)
     assert _rel(Cn.cpu().numpy(), Cn_ref) < CORR_TOL
+
+
+@pytest.mark.parametrize("tc", [1, 0])
+def test_colourless_nan_input_stays_local(ddp, env8, tc):
+    """A NaN in one spinor component at one site makes exactly the outputs of that time
+    slice that depend on it NaN; every other output stays finite and correct."""
+    ctx, gid = env8
+    box = ((0, 0, 0, 0), (2, 8, 8, 8))
+    did = ddp.ddp_set_domain(ctx, gid, *box)
+    m, bad = 4, 2
+    A = synth.random_spinor(m, oracle.box_sites(box[1]), 78)
+    A[bad, 700, 1, 2] = np.nan            # site 700 lies in the second time slice
+    X = torch.zeros((L8[0], m, m, m, 4), dtype=torch.complex128, device="cuda")
+    ddp.ddp_set_param(ctx, "colour_tensor_cores", tc)
+    try:
+        ddp.ddp_colourless_slices(ctx, did, _dev(A), m, 0, X)
+    finally:
+        ddp.ddp_set_param(ctx, "colour_tensor_cores", 1)
+        ddp.ddp_free_domain(ctx, did)
+    X = X.cpu().numpy()
+    clean = A.copy()
+    clean[bad, 700, 1, 2] = 0             # the outputs compared below do not depend on it
+    want = projector.colourless_spinors(L8, *box, clean)
+    # the diquark of a row with i or j = bad carries the NaN into every (k, alpha); an
+    # output column (k = bad, alpha) only when alpha is the NaN's spin
+    involved = np.zeros((m, m, m, 4), bool)
+    involved[bad] = involved[:, bad] = True
+    involved[:, :, bad, 1] = True
+    assert np.isnan(X[1][involved]).all()
+    assert np.isfinite(X[1][~involved]).all() and np.isfinite(X[0]).all()
+    assert _rel(X[1][~involved], want[1][~involved]) < TC_TOL
+    assert _rel(X[0], want[0]) < TC_TOL
