@@ -15,18 +15,18 @@
 // balanced base 128, a = 2^(e-7) sum_p q_p 2^(-7p) + O(2^(e-50)), q_0 in [-128, 128],
 // q_p in [-64, 63] for p > 0, each exact in BF16.  For every d < S the products of slices
 // p + q = d are summed on the tensor cores (tcgen05.mma kind::f16, BF16 operands,
-// FP32 accumulators in tensor memory, one per d).  Over KC = 256 reduction terms
-// every such sum is an integer of magnitude below 9 * 2^12 * 256 < 2^24, hence
+// FP32 accumulators in tensor memory, one per d).  Over KC = 448 reduction terms
+// every such sum is an integer of magnitude below 9 * 2^12 * 448 < 2^24, hence
 // exact in FP32; after each chunk the seven sums are converted to integers and
 // added exactly into two 64-bit fixed-point accumulators per output.  Products of
 // slices with p + q >= S are dropped: each term of the sum is exact to about
 // 2^-47 of its row maximum times its column maximum.
 //
-// Operands reach the tensor cores through a two-stage pipeline of bulk copies
+// Operands reach the tensor cores through a four-stage pipeline of bulk copies
 // (cp.async.bulk, completion on an mbarrier): the split kernels write every
-// (slice, 128- or 64-row tile, 32-deep K step) block contiguously in the
+// (slice, 128- or 64-row tile, 16-deep K step) block contiguously in the
 // shared-memory layout the MMA descriptor describes (K-major, no swizzle: 8-row x
-// 16-byte core matrices, 128 bytes apart along K, 512 bytes apart between 8-row
+// 16-byte core matrices, 128 bytes apart along K, 256 bytes apart between 8-row
 // groups), so that one copy per block stages it.
 #include <cmath>
 #include <cstring>
@@ -40,13 +40,14 @@ namespace {
 constexpr int S = 7;          // slices per operand; accumulator groups d = p + q < S
 constexpr int TM = 128;       // rows of A' per tile (the MMA's M)
 constexpr int TN = 64;        // rows of B' (output columns) per tile (the MMA's N)
-constexpr int KSTEP = 32;     // reduction depth per pipeline stage (two MMAs of K = 16)
-constexpr int CS = 8;         // stages per exact chunk: KC = 256
-constexpr int SBO = 512, LBO = 128;
+constexpr int KSTEP = 16;     // reduction depth per pipeline stage (one MMA of K = 16 per slice pair)
+constexpr int CS = 28;        // stages per exact chunk: KC = 448
+constexpr int SBO = 16 * KSTEP, LBO = 128;  // bytes between 8-row groups; between K core matrices
 constexpr int TILE_A = TM * KSTEP * 2, TILE_B = TN * KSTEP * 2;  // bytes
 constexpr int STAGE = S * (TILE_A + TILE_B);
-constexpr int NSTAGE = 2;
-constexpr int GEMM_THREADS = 512;
+constexpr int NSTAGE = 4;   // operand buffers in flight
+constexpr int GEMM_THREADS = 512;   // thread 0 streams the operands and issues the MMAs; all drain
+constexpr int GEMM_BLOCK = GEMM_THREADS;
 constexpr int DCOLS = TN / (GEMM_THREADS / 128);  // accumulator columns a thread drains
 constexpr int TMEM_COLS = 512;  // S * TN = 448 used
 constexpr int MAX_STEPS_PER_BLOCK = 1 << 16;  // keeps the fixed-point sums far below 2^63
@@ -55,6 +56,7 @@ constexpr int MMAX = 32;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 
 static_assert(S * TN <= TMEM_COLS, "accumulators exceed the tensor memory");
+static_assert(4 * TN <= 256, "one MMA spans at most four B slices (N <= 256)");
 static_assert(DCOLS == 16, "the drain loads 16 columns per thread");
 static_assert(CS * KSTEP * 9 * 4096 < (1 << 24), "chunk sums must stay exact in FP32");
 
@@ -65,8 +67,10 @@ __device__ __forceinline__ uint64_t mma_desc(uint32_t saddr) {
            ((uint64_t)((SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M = TM.
+__host__ __device__ constexpr uint32_t idesc_n(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
@@ -135,9 +139,32 @@ __device__ __forceinline__ double2 form_of(double2 v, int form, int spin) {
 // an infinity in the input turns the affected outputs into NaN (see k_ozaki_finish).
 __device__ __forceinline__ double mag(double v) { return isfinite(v) ? fabs(v) : (double)INFINITY; }
 
-__device__ __forceinline__ float2 df_of(double v) {
-    const float h = __double2float_rn(v);
-    return make_float2(h, __double2float_rn(v - (double)h));
+__device__ __forceinline__ float magf(float v) { return isfinite(v) ? fabsf(v) : INFINITY; }
+
+// 2^k as a float, -126 <= k <= 127.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// hi + lo = v 2^-f to 48 significant bits, from the bits of v by integer operations
+// (|v| < 2^f; parts below 2^-100 of 2^f, irrelevant at the 2^-49 precision of the
+// slices, are dropped; a non-finite v gives NaN).
+__device__ __forceinline__ float2 df_scaled(double v, int f) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ev = (int)((b >> 52) & 0x7FF);
+    if (ev == 0x7FF) return make_float2(NAN, NAN);
+    const int e = ev - 1023 - f;  // v 2^-f = 1.m 2^e
+    if (ev == 0 || e < -100) return make_float2(0.f, 0.f);
+    const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const unsigned long long mh = (m + (1ull << 28)) >> 29;  // the significand rounded to 24 bits
+    const long long rem = (long long)m - (long long)(mh << 29);  // |rem| <= 2^28
+    const float sc = pow2f(e - 23);
+    float hi = __uint2float_rn((unsigned)mh) * sc;                    // exact
+    float lo = (__ll2float_rn(rem) * 3.7252902984619140625e-9f) * sc;  // rem 2^-28 2^(e-23) ... 2^-1
+    lo *= 0.5f;                                                          // rem 2^(e-52)
+    if (b >> 63) {
+        hi = -hi;
+        lo = -lo;
+    }
+    return make_float2(hi, lo);
 }
 
 // (S, E) += sg * a * b for double-float a, b; (S, E) is an unnormalized sum.
@@ -211,27 +238,35 @@ struct EArgs {
 // from the spinors scaled by 2^-f_k (so that double-FP32 arithmetic keeps its range),
 // with the row maxima.  Block: ESITES sites, all rows; 16 consecutive threads share a row.
 __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
-    extern __shared__ float4 sh[];  // [m][ESITES][12]
+    extern __shared__ float4 sh[];  // [m][12][ESITES]: the site index fastest
+    __shared__ int fexp[MMAX];
     const int m = a.m;
     const int64_t x0 = (int64_t)blockIdx.x * ESITES;
     const int ns = (int)min((int64_t)ESITES, a.slice_n - x0);
+    for (int k = threadIdx.x; k < m; k += blockDim.x) fexp[k] = column_exponent(a.colmax, k);
+    __syncthreads();
     for (int e = threadIdx.x; e < m * ns * 12; e += blockDim.x) {
         const int c = e % 12, xs = (e / 12) % ns, k = e / (12 * ns);
-        const double sc = ldexp(1.0, -column_exponent(a.colmax, k));
-        const double2 v = form_of(a.A[((int64_t)k * a.n + a.site0 + x0 + xs) * 12 + c], a.form, c / 3);
-        const float2 re = df_of(v.x * sc), im = df_of(v.y * sc);
-        sh[(k * ESITES + xs) * 12 + c] = make_float4(re.x, re.y, im.x, im.y);
+        const double2 v = a.A[((int64_t)k * a.n + a.site0 + x0 + xs) * 12 + c];
+        float2 re = df_scaled(v.x, fexp[k]), im = df_scaled(v.y, fexp[k]);
+        // the form, exactly on the parts: 1 conj then g5 (spins 0, 1 negated), 2 negation
+        if (a.form == 1) im = make_float2(-im.x, -im.y);
+        if ((a.form == 1 && c < 6) || a.form == 2) {
+            re = make_float2(-re.x, -re.y);
+            im = make_float2(-im.x, -im.y);
+        }
+        sh[(k * 12 + c) * ESITES + xs] = make_float4(re.x, re.y, im.x, im.y);
     }
     __syncthreads();
     const int nit = a.rows * ESITES;
     for (int it0 = 0; it0 < nit; it0 += blockDim.x) {
         const int it = it0 + threadIdx.x;
         const int r = it / ESITES, xs = it % ESITES;
-        double mx = 0;
+        float mx = 0.f;
         if (r < a.rows && xs < ns) {
             int i, j;
             pair_of(r, m, i, j);
-            const float4 *si = sh + (i * ESITES + xs) * 12, *sj = sh + (j * ESITES + xs) * 12;
+            const float4 *si = sh + i * 12 * ESITES + xs, *sj = sh + j * 12 * ESITES + xs;
             float4 *o = a.E + (int64_t)r * 3 * a.slice_n + (x0 + xs) * 3;
             for (int c = 0; c < 3; c++) {
                 const int ca = (c + 1) % 3, cb = (c + 2) % 3;
@@ -241,18 +276,18 @@ __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
                 for (int t = 0; t < 2; t++) {
                     const float sg = t ? -1.f : 1.f;
                     const int p = t ? cb : ca, q = t ? ca : cb;
-                    dfc_mac(acc, si[3 + p], sj[q], sg);
-                    dfc_mac(acc, si[p], sj[3 + q], -sg);
-                    dfc_mac(acc, si[9 + p], sj[6 + q], sg);
-                    dfc_mac(acc, si[6 + p], sj[9 + q], -sg);
+                    dfc_mac(acc, si[(3 + p) * ESITES], sj[q * ESITES], sg);
+                    dfc_mac(acc, si[p * ESITES], sj[(3 + q) * ESITES], -sg);
+                    dfc_mac(acc, si[(9 + p) * ESITES], sj[(6 + q) * ESITES], sg);
+                    dfc_mac(acc, si[(6 + p) * ESITES], sj[(9 + q) * ESITES], -sg);
                 }
                 const float2 R = df_norm(acc[0], acc[1]), I = df_norm(acc[2], acc[3]);
                 o[c] = make_float4(-I.x, -I.y, R.x, R.y);  // times i
-                mx = fmax(mx, fmax(mag(R.x), mag(I.x)));
+                mx = fmaxf(mx, fmaxf(magf(R.x), magf(I.x)));
             }
         }
-        for (int off = 8; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        if ((threadIdx.x & 15) == 0 && r < a.rows && mx > 0) atomic_max_pos(a.rowmax + r, mx);
+        for (int off = 8; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if ((threadIdx.x & 15) == 0 && r < a.rows && mx > 0.f) atomic_max_pos(a.rowmax + r, (double)mx);
     }
 }
 
@@ -299,8 +334,9 @@ __device__ __forceinline__ void digits7(long long N, __nv_bfloat16 out[S]) {
 
 // (row rl, depth kl) of element e of one tile block in the MMA's shared-memory layout.
 __device__ __forceinline__ void tile_pos(int e, int &rl, int &kl) {
-    rl = ((e >> 3) & 7) + 8 * (e >> 8);
-    kl = (e & 7) + 8 * ((e >> 6) & 3);
+    constexpr int KC8 = KSTEP / 8;  // core matrices along K
+    rl = ((e >> 3) & 7) + 8 * (e / (64 * KC8));
+    kl = (e & 7) + 8 * ((e >> 6) % KC8);
 }
 
 struct SplitArgs {
@@ -310,7 +346,7 @@ struct SplitArgs {
     int m, form, rows;
     int MT, NT, KSh;      // tiles; K steps of one half (Re / Im) of the reduction
     const double *rowmax, *colmax;
-    __nv_bfloat16 *Aq, *Bq;  // [S][MT][2 KSh][128 x 32], [S][NT][2 KSh][64 x 32]
+    __nv_bfloat16 *Aq, *Bq;  // [MT][2 KSh][S][128 x KSTEP], [NT][2 KSh][S][64 x KSTEP]
 };
 
 // A' = [Re E | Im E]: thread per (row, kx), writes the slices of both halves.  With
@@ -335,11 +371,12 @@ __global__ void k_split_A(SplitArgs a) {
     } else {
         for (int p = 0; p < S; p++) re[p] = im[p] = __double2bfloat16(0.0);
     }
+    // tile block (mt, K step, slice): the S slices of one step lie contiguously
     const int KS = 2 * a.KSh;
+    const int64_t bre = ((int64_t)mt * KS + ksr) * S, bim = ((int64_t)mt * KS + a.KSh + ksr) * S;
     for (int p = 0; p < S; p++) {
-        const int64_t base = ((int64_t)p * a.MT + mt) * KS;
-        a.Aq[(base + ksr) * (TM * KSTEP) + e] = re[p];
-        a.Aq[(base + a.KSh + ksr) * (TM * KSTEP) + e] = im[p];
+        a.Aq[(bre + p) * (TM * KSTEP) + e] = re[p];
+        a.Aq[(bim + p) * (TM * KSTEP) + e] = im[p];
     }
 }
 
@@ -370,10 +407,10 @@ __global__ void k_split_B(SplitArgs a) {
         for (int p = 0; p < S; p++) lo[p] = hi[p] = __double2bfloat16(0.0);
     }
     const int KS = 2 * a.KSh;
+    const int64_t blo = ((int64_t)nt * KS + ksr) * S, bhi = ((int64_t)nt * KS + a.KSh + ksr) * S;
     for (int p = 0; p < S; p++) {
-        const int64_t base = ((int64_t)p * a.NT + nt) * KS;
-        a.Bq[(base + ksr) * (TN * KSTEP) + e] = lo[p];
-        a.Bq[(base + a.KSh + ksr) * (TN * KSTEP) + e] = hi[p];
+        a.Bq[(blo + p) * (TN * KSTEP) + e] = lo[p];
+        a.Bq[(bhi + p) * (TN * KSTEP) + e] = hi[p];
     }
 }
 
@@ -393,10 +430,22 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
                  : "memory");
 }
 
+// Barrier 1 over the GEMM_THREADS threads; returns the OR of v over them.
+__device__ __forceinline__ bool drain_barrier_or(bool v) {
+    uint32_t r;
+    asm volatile("{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n"
+                 " barrier.cta.red.or.pred po, 1, %2, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "n"(GEMM_THREADS)
+                 : "memory");
+    return r != 0;
+}
+
 // One CTA per (128-row tile, 64-column tile, K range).  Thread 0 streams the operand
-// blocks and issues the MMAs; after every CS stages all sixteen warps drain the seven
-// accumulators (warp w: lanes 32 (w % 4) .. + 31, columns DCOLS (w / 4) .. + DCOLS - 1).
-__global__ void __launch_bounds__(GEMM_THREADS, 1) k_ozaki_gemm(GemmArgs a) {
+// blocks of each K step into NSTAGE buffers (two bulk copies per step) and issues the
+// MMAs; after every CS steps the sixteen warps drain the seven accumulators (warp w: lanes 32 (w % 4) .. + 31, columns DCOLS (w / 4) .. + DCOLS - 1)
+// into exact 64-bit fixed point.
+__global__ void __launch_bounds__(GEMM_BLOCK, 1) k_ozaki_gemm(GemmArgs a) {
     extern __shared__ __align__(128) uint8_t dsm[];
     __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE];
     __shared__ uint32_t tbase;
@@ -422,120 +471,127 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_ozaki_gemm(GemmArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tbase;
 
-    auto load = [&](int j) {  // thread 0: K step s0 + j into buffer j % 2
-        const int st = j & 1;
-        const uint32_t sa = smem_u32(dsm + st * STAGE), sb = sa + S * TILE_A;
-        const uint32_t fb = smem_u32(&full[st]);
+    auto load = [&](int q) {  // thread 0: K step s0 + q into buffer q % NSTAGE (two bulk copies)
+        const int st = q % NSTAGE;
+        const uint32_t sa = smem_u32(dsm + st * STAGE), fb = smem_u32(&full[st]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"((uint32_t)STAGE)
                      : "memory");
-        for (int p = 0; p < S; p++) {
-            bulk_copy(sa + p * TILE_A, a.Aq + (((int64_t)p * a.MT + mt) * a.KS + s0 + j) * TILE_A, TILE_A, fb);
-            bulk_copy(sb + p * TILE_B, a.Bq + (((int64_t)p * a.NT + nt) * a.KS + s0 + j) * TILE_B, TILE_B, fb);
-        }
+        bulk_copy(sa, a.Aq + (((int64_t)mt * a.KS + s0 + q) * S) * TILE_A, S * TILE_A, fb);
+        bulk_copy(sa + S * TILE_A, a.Bq + (((int64_t)nt * a.KS + s0 + q) * S) * TILE_B, S * TILE_B, fb);
     };
-
-    int64_t acc_hi[DCOLS], acc_lo[DCOLS];  // 2^14 sum_{d<=2} 2^-7d G_d and 2^42 sum_{d>=3} 2^-7d G_d
+    {
+        // ---- MMA issue (thread 0) and accumulator drain (GEMM_THREADS threads)
+        int64_t acc_hi[DCOLS], acc_lo[DCOLS];  // 2^14 sum_{d<=2} 2^-7d G_d and 2^42 sum_{d>=3} 2^-7d G_d
 #pragma unroll
-    for (int c = 0; c < DCOLS; c++) acc_hi[c] = acc_lo[c] = 0;
-    int pend_load = -1, pend_mma = -1;  // thread 0: a copy or MMAs not yet waited for
-    bool ok = true, aborted = false;
-    if (tid == 0 && nsteps > 0) {
-        load(0);
-        pend_load = 0;
-    }
-    for (int j = 0; j < nsteps; j++) {
-        const int st = j & 1;
-        if (tid == 0 && ok) {
-            ok = mbar_wait(smem_u32(&full[st]), (j >> 1) & 1);
-            if (ok) {
-                pend_load = -1;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sa = smem_u32(dsm + st * STAGE), sb = sa + S * TILE_A;
-                for (int p = 0; p < S; p++)
-                    for (int q = 0; p + q < S; q++) {
-                        const uint32_t dcol = tmem + (uint32_t)((p + q) * TN);
+        for (int c = 0; c < DCOLS; c++) acc_hi[c] = acc_lo[c] = 0;
+        bool ok = true, aborted = false;
+        // thread 0: the last step loaded, the last step whose operands arrived, the last
+        // step whose MMAs were committed
+        int loaded = -1, consumed = -1, pend_mma = -1;
+        if (tid == 0)
+            for (int q = 0; q < NSTAGE - 1 && q < nsteps; q++) {
+                load(q);
+                loaded = q;
+            }
+        for (int j = 0; j < nsteps; j++) {
+            const int st = j % NSTAGE;
+            if (tid == 0 && ok) {
+                ok = mbar_wait(smem_u32(&full[st]), (j / NSTAGE) & 1);
+                if (ok) {
+                    consumed = j;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_u32(dsm + st * STAGE), sb = sa + S * TILE_A;
+                    const uint64_t da0 = mma_desc(sa), db0 = mma_desc(sb);
+                    // The B slices of a stage lie one after another along N, so one MMA of
+                    // A slice p against B slices q0 .. q0 + nq - 1 (N = 64 nq <= 256) writes the
+                    // adjacent accumulators of the groups p + q0 .. p + q0 + nq - 1.
 #pragma unroll
-                        for (int kk = 0; kk < KSTEP / 16; kk++) {
-                            const uint64_t da = mma_desc(sa + p * TILE_A + kk * 2 * LBO);
-                            const uint64_t db = mma_desc(sb + q * TILE_B + kk * 2 * LBO);
-                            // the first product of each group in a chunk overwrites the accumulator
-                            const uint32_t accum = (j % CS == 0 && p == 0 && kk == 0) ? 0u : 1u;
+                    for (int p = 0; p < S; p++) {
+#pragma unroll
+                        for (int q0 = 0; q0 < S - p; q0 += 4) {
+                            const int nq = (S - p - q0) < 4 ? (S - p - q0) : 4;
+                            const uint32_t dcol = tmem + (uint32_t)((p + q0) * TN);
+                            const uint64_t da = da0 + (uint64_t)((p * TILE_A) >> 4);
+                            const uint64_t db = db0 + (uint64_t)((q0 * TILE_B) >> 4);
+                            // the first products of a chunk (p = 0 covers every group) overwrite
+                            const uint32_t accum = (j % CS == 0 && p == 0) ? 0u : 1u;
                             asm volatile("{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
                                          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n"
-                                         ::"r"(dcol), "l"(da), "l"(db), "r"(IDESC), "r"(accum)
+                                         ::"r"(dcol), "l"(da), "l"(db), "r"(idesc_n(TN * nq)), "r"(accum)
                                          : "memory");
                         }
                     }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             ::"r"(smem_u32(&empty[st]))
-                             : "memory");
-                pend_mma = j;
-                if (j + 1 < nsteps) {
-                    // the other buffer is free once the MMAs of step j - 1 have read it
-                    if (j >= 1) ok = mbar_wait(smem_u32(&empty[st ^ 1]), ((j - 1) >> 1) & 1);
-                    if (ok) {
-                        load(j + 1);
-                        pend_load = j + 1;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(smem_u32(&empty[st]))
+                                 : "memory");
+                    pend_mma = j;
+                    const int nxt = j + NSTAGE - 1;
+                    if (nxt < nsteps) {
+                        // its buffer is free once the MMAs of step j - 1 have read it
+                        if (j >= 1) ok = mbar_wait(smem_u32(&empty[(j - 1) % NSTAGE]), ((j - 1) / NSTAGE) & 1);
+                        if (ok) {
+                            load(nxt);
+                            loaded = nxt;
+                        }
                     }
                 }
+                if (!ok) atomicExch(a.err, 1);
             }
-            if (!ok) atomicExch(a.err, 1);
-        }
-        if (j % CS == CS - 1 || j == nsteps - 1) {
-            // every thread takes the same branch: the barrier returns the OR of the failures
-            if (__syncthreads_or(tid == 0 && !ok)) {
-                aborted = true;
-                break;
-            }
-            const bool done = mbar_wait(smem_u32(&empty[st]), (j >> 1) & 1);
-            if (!done) atomicExch(a.err, 1);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (done) {
-                const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-                const int cbase = DCOLS * (warp >> 2);
+            if (j % CS == CS - 1 || j == nsteps - 1) {
+                // every draining thread takes the same branch: the barrier returns the OR
+                if (drain_barrier_or(tid == 0 && !ok)) {
+                    aborted = true;
+                    break;
+                }
+                const bool done = mbar_wait(smem_u32(&empty[st]), (j / NSTAGE) & 1);
+                if (!done) atomicExch(a.err, 1);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (done) {
+                    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+                    const int cbase = DCOLS * (warp >> 2);
 #pragma unroll
-                for (int d = 0; d < S; d++) {
-                    uint32_t r[DCOLS];
-                    const uint32_t taddr = tmem + lane_base + (uint32_t)(d * TN + cbase);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-                        " [%16];"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                          "=r"(r[14]), "=r"(r[15])
-                        : "r"(taddr)
-                        : "memory");
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    // G_d is an integer below 2^24: the conversion is exact
-                    const int sh = d <= 2 ? 14 - 7 * d : 42 - 7 * d;
+                    for (int d = 0; d < S; d++) {
+                        uint32_t r[DCOLS];
+                        const uint32_t taddr = tmem + lane_base + (uint32_t)(d * TN + cbase);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                            "%15}, [%16];"
+                            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                              "=r"(r[14]), "=r"(r[15])
+                            : "r"(taddr)
+                            : "memory");
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        // G_d is an integer below 2^24: the conversion is exact
+                        const int sh = d <= 2 ? 14 - 7 * d : 42 - 7 * d;
 #pragma unroll
-                    for (int c = 0; c < DCOLS; c++) {
-                        const int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[c])) * (int64_t)(1ll << sh);
-                        if (d <= 2)
-                            acc_hi[c] += v;
-                        else
-                            acc_lo[c] += v;
+                        for (int c = 0; c < DCOLS; c++) {
+                            const int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[c])) * (int64_t)(1ll << sh);
+                            if (d <= 2)
+                                acc_hi[c] += v;
+                            else
+                                acc_lo[c] += v;
+                        }
                     }
                 }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            if (__syncthreads_or(!done)) {
-                aborted = true;
-                break;
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                if (drain_barrier_or(!done)) {
+                    aborted = true;
+                    break;
+                }
             }
         }
-    }
-    if (tid == 0) {
-        // after a failed wait: give the copies and MMAs in flight a bounded time to land
-        if (pend_mma >= 0) mbar_wait(smem_u32(&empty[pend_mma & 1]), (pend_mma >> 1) & 1);
-        if (pend_load >= 0) mbar_wait(smem_u32(&full[pend_load & 1]), (pend_load >> 1) & 1);
-    }
-    __syncthreads();
-    if (!aborted) {
-        const int row = mt * TM + 32 * (warp & 3) + lane;
-        double *o = a.part + ((int64_t)z * a.MT * TM + row) * a.ncols + nt * TN + DCOLS * (warp >> 2);
+        if (tid == 0) {
+            // after a failed wait: give the copies and MMAs in flight a bounded time to land
+            if (pend_mma >= 0) mbar_wait(smem_u32(&empty[pend_mma % NSTAGE]), (pend_mma / NSTAGE) & 1);
+            for (int q = consumed + 1; q <= loaded; q++) mbar_wait(smem_u32(&full[q % NSTAGE]), (q / NSTAGE) & 1);
+        }
+        if (!aborted) {
+            const int row = mt * TM + 32 * (warp & 3) + lane;
+            double *o = a.part + ((int64_t)z * a.MT * TM + row) * a.ncols + nt * TN + DCOLS * (warp >> 2);
 #pragma unroll
-        for (int c = 0; c < DCOLS; c++) o[c] = ldexp((double)acc_hi[c], -14) + ldexp((double)acc_lo[c], -42);
+            for (int c = 0; c < DCOLS; c++) o[c] = ldexp((double)acc_hi[c], -14) + ldexp((double)acc_lo[c], -42);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -655,7 +711,7 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
         g.ncols = ncols;
         g.part = part;
         g.err = err;
-        k_ozaki_gemm<<<dim3(MT, NT, ksplit), GEMM_THREADS, gsm, st>>>(g);
+        k_ozaki_gemm<<<dim3(MT, NT, ksplit), GEMM_BLOCK, gsm, st>>>(g);
         const int64_t nx = (int64_t)rows * Q;
         k_ozaki_finish<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(
             part, ksplit, prow, ncols, m, rows, rowmax, colmax, X + (int64_t)((o0 + z) % L0) * m * m * Q);
