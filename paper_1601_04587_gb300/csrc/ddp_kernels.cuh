@@ -37,7 +37,8 @@ struct LoopCtl {
     int n_active;
     int iter;
     int maxit;
-    int pad;
+    int pad;          // host-polled loop: 1 while the loop continues
+    int done_blocks;  // blocks of k_fin<FIN_RHO> finished in this iteration
 };
 
 // Reduction partial buffers: complex and real, per (item, column, tile).
@@ -252,7 +253,12 @@ __device__ __forceinline__ void get_link(const R *d, cx<R> u[3][3]) {
 
 
 template <class P, int EPI, int DOT, bool CLOV = false>
-__global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : 3) k_hop(HopArgs a) {
+// Resident blocks per SM the register budget of the 32- and 16-bit stencils is fitted to
+// (3: 56 registers a thread; 2: 80).
+#ifndef DDP_HOP_MINB
+#define DDP_HOP_MINB 3
+#endif
+__global__ void __launch_bounds__(384, sizeof(typename P::real) == 8 ? 1 : DDP_HOP_MINB) k_hop(HopArgs a) {
     using R = typename P::real;
     constexpr int TSMAX = HOP_TS;
     __shared__ Item it;
@@ -575,6 +581,10 @@ struct FinArgs {
     int nsolve;
     Partials A, B;  // B used by FIN_BNORM / FIN_RESID (odd parity)
     LoopCtl *ctl;
+    // FIN_RHO ends an inner-loop iteration: its last block to finish also runs the loop
+    // control (0: not in a loop; 1: sets the graph's WHILE condition; 2: host-polled)
+    int loop_mode;
+    cudaGraphConditionalHandle loop;
 };
 
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
@@ -698,23 +708,23 @@ __global__ void __launch_bounds__(256) k_fin(FinArgs a) {
                 atomicAdd(&a.ctl->n_active, 1);
             }
         }
+        if (a.loop_mode) {
+            // the last solve's block decides whether the loop goes on (every block's
+            // n_active increment is ordered before its arrival by the fence)
+            __threadfence();
+            if (atomicAdd(&a.ctl->done_blocks, 1) == a.nsolve - 1) {
+                __threadfence();
+                LoopCtl *c = a.ctl;
+                const int cont = (atomicAdd(&c->n_active, 0) > 0) && (++c->iter < c->maxit);
+                c->n_active = 0;
+                c->done_blocks = 0;
+                if (a.loop_mode == 1)
+                    cudaGraphSetConditional(a.loop, cont ? 1u : 0u);
+                else
+                    c->pad = cont;
+            }
+        }
     }
-}
-
-// Loop controller of the device-driven inner loop: continue while any solve
-// is active and the global iteration cap is not reached.
-static __global__ void k_loop_ctl(LoopCtl *ctl, cudaGraphConditionalHandle h) {
-    int cont = (ctl->n_active > 0) && (++ctl->iter < ctl->maxit);
-    ctl->n_active = 0;
-    cudaGraphSetConditional(h, cont ? 1u : 0u);
-}
-
-// Host-polled variant (no conditional node): the same bookkeeping, the host
-// reads ctl->pad as the continue flag.
-static __global__ void k_loop_ctl_host(LoopCtl *ctl) {
-    int cont = (ctl->n_active > 0) && (++ctl->iter < ctl->maxit);
-    ctl->n_active = 0;
-    ctl->pad = cont;
 }
 
 // ---------------------------------------------- user layout <-> even-odd fields

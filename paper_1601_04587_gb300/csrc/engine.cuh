@@ -40,6 +40,8 @@ struct Engine {
     Item *d_items = nullptr;
     SolveState *d_st = nullptr;
     LoopCtl *d_ctl = nullptr;
+    int loop_mode = 0;  // how the iteration body being captured ends (see FinArgs)
+    cudaGraphConditionalHandle loop_handle = 0;
     std::vector<SolveState> h_st;
     Launch L;
     int threads = 0;
@@ -102,6 +104,8 @@ struct Engine {
         a.A = A;
         a.B = B;
         a.ctl = d_ctl;
+        a.loop_mode = FIN == FIN_RHO ? loop_mode : 0;
+        a.loop = loop_handle;
         k_fin<FIN><<<plan.nsolve, 256, 0, ctx->stream>>>(a);
         launches++;
     }
@@ -176,18 +180,19 @@ struct Engine {
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             DDP_CUDA(ctx, cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
                                                         cudaStreamCaptureModeThreadLocal));
-            iteration_body();
-            k_loop_ctl<<<1, 1, 0, st>>>(d_ctl, h);
+            loop_mode = 1;
+            loop_handle = h;
+            iteration_body();  // its last kernel sets the loop condition
+            loop_mode = 0;
             cudaGraph_t captured;
             cudaError_t e = cudaStreamEndCapture(st, &captured);
             if (e != cudaSuccess) return set_cuda_error(ctx, e, "capture of the inner loop");
             DDP_CUDA(ctx, cudaGraphInstantiate(&loop_exec, loop_graph, 0));
         } else {
             DDP_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            for (int i = 0; i < ctx->prm.host_chunk; i++) {
-                iteration_body();
-                k_loop_ctl_host<<<1, 1, 0, st>>>(d_ctl);
-            }
+            loop_mode = 2;
+            for (int i = 0; i < ctx->prm.host_chunk; i++) iteration_body();
+            loop_mode = 0;
             cudaError_t e = cudaStreamEndCapture(st, &loop_graph);
             if (e != cudaSuccess) return set_cuda_error(ctx, e, "capture of the inner loop");
             DDP_CUDA(ctx, cudaGraphInstantiate(&loop_exec, loop_graph, 0));
@@ -196,8 +201,9 @@ struct Engine {
     }
 
     int run_inner() {
-        // body launches per iteration: 4 hops + 4 vector updates... counted after the loop
-        const long per_iter = 11;
+        // launches per iteration: 4 stencils, 3 vector updates, 3 scalar-recurrence
+        // kernels (the last of which also runs the loop control)
+        const long per_iter = 10;
         if (ctx->prm.use_conditional) {
             DDP_CUDA(ctx, cudaGraphLaunch(loop_exec, ctx->stream));
         } else {
@@ -264,7 +270,7 @@ struct Engine {
                                       cudaMemcpyHostToDevice, st));
         DDP_CUDA(ctx, cudaMemcpyAsync(d_st, h_st.data(), plan.nsolve * sizeof(SolveState), cudaMemcpyHostToDevice,
                                       st));
-        LoopCtl c0 = {0, 0, ctx->prm.max_inner, 0};
+        LoopCtl c0 = {0, 0, ctx->prm.max_inner, 0, 0};
         DDP_CUDA(ctx, cudaMemcpyAsync(d_ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
         return DDP_OK;
     }
