@@ -303,7 +303,10 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * "tile_cols" (columns per block, 1..12, 0 = automatic), "tuned_cols_fp64" ...
  * "tuned_cols_bf16" (a remembered autotuner choice, 0 = none), "conditional" (1: the
  * inner loop is a device-driven CUDA-graph WHILE node; 0: host-polled graph
- * chunks).  DDP_ERR_INVALID_ARG for unknown names or values. */
+ * chunks), "projector_tensor_cores" (1, the default: the Gram blocks and colourless
+ * spinor sums of the projector cut, m <= 32, run as an emulated-FP64 product on the
+ * tensor cores; 0: direct FP64 kernels).  DDP_ERR_INVALID_ARG for unknown names or
+ * values. */
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value);
 
 /* Inner-loop stencil variants, for ddp_time_hop: one BiCGStab iteration on the
@@ -352,7 +355,13 @@ int ddp_serve_reset(ddp_ctx *ctx);
  *   nucleon: X = ddp_colourless_slices(Gbar, u, form 1), Y = ddp_colourless_slices(G*, w,
  *            form 2), ddp_projected_nucleon(X, Y)              (Eq. W0tbary).
  * Fields: [m][n_sites][4][3] complex in domain-local order, host or device memory
- * (detected per pointer); every call returns when its output is complete. */
+ * (detected per pointer); every call returns when its output is complete.
+ * Gram blocks and colourless sums (m <= 32) run on the tensor cores: every operand is
+ * split into seven 7-bit integer slices under a power-of-two exponent per row or
+ * column, the slice products are summed exactly, and each term of a sum is exact to
+ * about 2^-47 of its row maximum times its column maximum (FP64-level; the parameter
+ * "projector_tensor_cores" = 0 selects direct FP64 kernels).  A NaN or infinity in an
+ * input makes exactly the outputs of its time slice that depend on it NaN. */
 
 /* V <- the orthonormal basis of span(V) that Gram-Schmidt in column order gives
  * (Cholesky QR, twice, in FP64).  DDP_ERR_INVALID_ARG if the columns are linearly

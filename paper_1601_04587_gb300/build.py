@@ -12,7 +12,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libddp.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["api.cu", "contract.cu", "serve.cu", "clover.cu", "projector.cu", "colour_tc.cu", "solve_f64.cu", "solve_f32.cu", "solve_f16.cu", "solve_bf16.cu"]
+SOURCES = ["api.cu", "contract.cu", "serve.cu", "clover.cu", "projector.cu", "projector_tc.cu", "solve_f64.cu", "solve_f32.cu", "solve_f16.cu", "solve_bf16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -80,7 +80,7 @@ struct EngineParams {
     int CG_prec[4] = {0, 0, 0, 0};  // columns per block chosen by ddp_autotune, per storage format
     int use_conditional = 1;    // device-driven while loop in a CUDA graph
     int host_chunk = 16;        // iterations per host check without conditional nodes
-    int colour_tc = 1;          // colourless-spinor sums on the tensor cores (0: direct FP64 kernel)
+    int proj_tc = 1;            // projector-cut Gram blocks and colourless sums on the tensor cores (0: FP64 kernels)
 };
 
 // A growable device arena owned by the context.
@@ -152,6 +152,8 @@ int clover_for(ddp_ctx *ctx, GaugeDev &g, double kappa, double csw, const Clover
 // Colourless-spinor time-slice sums on the tensor cores (device fields; X zeroed by the caller).
 int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, int64_t slice_n, int nslice, int o0,
                   int L0, double2 *X);
+// Gram blocks of nseg row segments on the tensor cores (m <= 32; device buffers).
+int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int nseg, double2 *out);
 
 #define DDP_CUDA(ctx, call)                                          \
     do {                                                            \

@@ -94,7 +94,9 @@ __global__ void k_gram_reduce(const double2 *part, int nks, int m, int nseg, dou
 }
 
 // Gram blocks of nseg consecutive row segments of seg rows each; out [nseg][m][m].
+// On the tensor cores (gram_tc) unless the context asks for the FP64 kernel or m > 32.
 int gram(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int nseg, double2 *out, Arena &ar) {
+    if (ctx->prm.proj_tc && m <= 32) return gram_tc(ctx, A, cs, m, seg, nseg, out);
     const int ntile = (m + GT - 1) / GT;
     // enough blocks to fill the GPU: split each segment into pieces of >= 512 rows
     int64_t want = std::max<int64_t>(1, 1200 / std::max<int64_t>(1, (int64_t)ntile * ntile * nseg));
@@ -640,7 +642,7 @@ int ddp_colourless_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, i
     if ((rc = ba.init(ctx, A, (size_t)m * d->n * 12 * sizeof(double2), true))) return rc;
     if ((rc = bo.init(ctx, X_out, (size_t)L0 * per * sizeof(double2), false))) return rc;
     DDP_CUDA(ctx, cudaMemsetAsync(bo.dev, 0, (size_t)L0 * per * sizeof(double2), ctx->stream));
-    if (ctx->prm.colour_tc) {
+    if (ctx->prm.proj_tc) {
         rc = colourless_tc(ctx, (const double2 *)ba.dev, d->n, m, form, slice_n, d->e[0], d->o[0], L0,
                            (double2 *)bo.dev);
         if (rc) return rc;

@@ -1,7 +1,9 @@
-// Time-slice sums of the colourless spinors (Sec. 5, Eq. W0tbary) on the tensor
-// cores with FP64-level accuracy.
+// The two contraction-shaped steps of the projector-cut factorization (Sec. 5) on the
+// tensor cores with FP64-level accuracy: the time-slice sums of the colourless spinors
+// (Eq. W0tbary) and the Gram blocks conj(A_i) . A_j (the pion blocks of Eq. Bpions and
+// the Cholesky QR of the inverse iteration), both as one emulated-FP64 product kernel.
 //
-// Per time slice the sum is a complex matrix product
+// Colourless spinors.  Per time slice the sum is a complex matrix product
 //   X[(i,j)][(k,alpha)] = sum_{(x,c)} E[(i,j)][(x,c)] s_k(x)_{alpha c},
 //   E[(i,j)][(x,c)] = sum_{ab} eps_abc (s_i^a)^T C g5 s_j^b          (the diquark, FP64).
 // C g5 is antisymmetric, so E is symmetric in (i, j): only the m(m+1)/2 rows i <= j
@@ -418,6 +420,7 @@ __global__ void k_split_B(SplitArgs a) {
 
 struct GemmArgs {
     const uint8_t *Aq, *Bq;
+    int a_bytes;      // bytes of one A slice block per K step: TILE_A, or fewer rows (see gram_tc)
     int MT, NT, KS, ksplit;
     int ncols;        // NT * TN
     double *part;     // [ksplit][MT * TM][ncols]: sum_d 2^-7d G_d of this block's K range
@@ -474,14 +477,18 @@ __global__ void __launch_bounds__(GEMM_BLOCK, 1) k_ozaki_gemm(GemmArgs a) {
     auto load = [&](int q) {  // thread 0: K step s0 + q into buffer q % NSTAGE (two bulk copies)
         const int st = q % NSTAGE;
         const uint32_t sa = smem_u32(dsm + st * STAGE), fb = smem_u32(&full[st]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"((uint32_t)STAGE)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                     "r"((uint32_t)(S * (a.a_bytes + TILE_B)))
                      : "memory");
-        bulk_copy(sa, a.Aq + (((int64_t)mt * a.KS + s0 + q) * S) * TILE_A, S * TILE_A, fb);
-        bulk_copy(sa + S * TILE_A, a.Bq + (((int64_t)nt * a.KS + s0 + q) * S) * TILE_B, S * TILE_B, fb);
+        bulk_copy(sa, a.Aq + (((int64_t)mt * a.KS + s0 + q) * S) * a.a_bytes, S * a.a_bytes, fb);
+        bulk_copy(sa + S * a.a_bytes, a.Bq + (((int64_t)nt * a.KS + s0 + q) * S) * TILE_B, S * TILE_B, fb);
     };
     {
         // ---- MMA issue (thread 0) and accumulator drain (GEMM_THREADS threads)
-        int64_t acc_hi[DCOLS], acc_lo[DCOLS];  // 2^14 sum_{d<=2} 2^-7d G_d and 2^42 sum_{d>=3} 2^-7d G_d
+        // 2^14 sum_{d<=2} 2^-7d G_d and 2^42 sum_{d>=3} 2^-7d G_d in two's complement (unsigned
+        // arithmetic: exact for every accumulator row that holds a result, and defined
+        // modulo 2^64 for the padding rows, whose values are discarded)
+        uint64_t acc_hi[DCOLS], acc_lo[DCOLS];
 #pragma unroll
         for (int c = 0; c < DCOLS; c++) acc_hi[c] = acc_lo[c] = 0;
         bool ok = true, aborted = false;
@@ -500,7 +507,10 @@ __global__ void __launch_bounds__(GEMM_BLOCK, 1) k_ozaki_gemm(GemmArgs a) {
                 if (ok) {
                     consumed = j;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sa = smem_u32(dsm + st * STAGE), sb = sa + S * TILE_A;
+                    // A slices a_bytes apart: with fewer than 128 rows stored, the MMA's
+                    // remaining rows read whatever follows and only feed accumulator rows
+                    // that are never drained into results
+                    const uint32_t sa = smem_u32(dsm + st * STAGE), sb = sa + S * a.a_bytes;
                     const uint64_t da0 = mma_desc(sa), db0 = mma_desc(sb);
                     // The B slices of a stage lie one after another along N, so one MMA of
                     // A slice p against B slices q0 .. q0 + nq - 1 (N = 64 nq <= 256) writes the
@@ -511,7 +521,7 @@ __global__ void __launch_bounds__(GEMM_BLOCK, 1) k_ozaki_gemm(GemmArgs a) {
                         for (int q0 = 0; q0 < S - p; q0 += 4) {
                             const int nq = (S - p - q0) < 4 ? (S - p - q0) : 4;
                             const uint32_t dcol = tmem + (uint32_t)((p + q0) * TN);
-                            const uint64_t da = da0 + (uint64_t)((p * TILE_A) >> 4);
+                            const uint64_t da = da0 + (uint64_t)((p * a.a_bytes) >> 4);
                             const uint64_t db = db0 + (uint64_t)((q0 * TILE_B) >> 4);
                             // the first products of a chunk (p = 0 covers every group) overwrite
                             const uint32_t accum = (j % CS == 0 && p == 0) ? 0u : 1u;
@@ -566,7 +576,7 @@ __global__ void __launch_bounds__(GEMM_BLOCK, 1) k_ozaki_gemm(GemmArgs a) {
                         const int sh = d <= 2 ? 14 - 7 * d : 42 - 7 * d;
 #pragma unroll
                         for (int c = 0; c < DCOLS; c++) {
-                            const int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[c])) * (int64_t)(1ll << sh);
+                            const uint64_t v = (uint64_t)(int64_t)__float2int_rn(__uint_as_float(r[c])) << sh;
                             if (d <= 2)
                                 acc_hi[c] += v;
                             else
@@ -590,7 +600,8 @@ __global__ void __launch_bounds__(GEMM_BLOCK, 1) k_ozaki_gemm(GemmArgs a) {
             const int row = mt * TM + 32 * (warp & 3) + lane;
             double *o = a.part + ((int64_t)z * a.MT * TM + row) * a.ncols + nt * TN + DCOLS * (warp >> 2);
 #pragma unroll
-            for (int c = 0; c < DCOLS; c++) o[c] = ldexp((double)acc_hi[c], -14) + ldexp((double)acc_lo[c], -42);
+            for (int c = 0; c < DCOLS; c++)
+                o[c] = ldexp((double)(int64_t)acc_hi[c], -14) + ldexp((double)(int64_t)acc_lo[c], -42);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -704,6 +715,7 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
         GemmArgs g;
         g.Aq = Aq;
         g.Bq = Bq;
+        g.a_bytes = TILE_A;
         g.MT = MT;
         g.NT = NT;
         g.KS = KS;
@@ -723,6 +735,186 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
     DDP_CUDA(ctx, cudaStreamSynchronize(st));
     if (h) {
         snprintf(ctx->last_error, sizeof(ctx->last_error), "colourless spinors: a wait for the tensor cores gave up");
+        return DDP_ERR_CUDA;
+    }
+    return DDP_OK;
+}
+
+}  // namespace ddp
+
+// ------------------------------------------------------------ Gram blocks
+//
+// G[i][j] = sum_r conj(A_i[r]) A_j[r] over the rows r of one segment, on the same
+// emulated-FP64 product: A' rows i = [Re A_i | Im A_i], B' rows = [Re A_j | Im A_j]
+// (the real parts, columns j < m) and [Im A_j | -Re A_j] (the imaginary parts,
+// m <= c < 2m), every row and column with its own power-of-two exponent.  The m <= 32
+// rows of A' are stored as R8 = 8 ceil(m / 8) rows per block (the MMA's other rows read
+// whatever follows in shared memory and feed accumulator rows that are never used).
+
+namespace {
+
+// colmax[i] = max over the segment's rows of |Re A_i|, |Im A_i|
+__global__ void __launch_bounds__(256) k_gram_max(const double2 *A, int64_t cs, int m, int64_t r0, int64_t nrow,
+                                                  double *colmax) {
+    const int i = blockIdx.y;
+    double mx = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrow; r += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = A[(int64_t)i * cs + r0 + r];
+        mx = fmax(mx, fmax(mag(v.x), mag(v.y)));
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomic_max_pos(colmax + i, mx);
+    (void)m;
+}
+
+struct GramSplitArgs {
+    const double2 *A;
+    int64_t cs, r0, nrow;  // column stride; the segment's rows
+    int m, R8, KSh;
+    const double *colmax;
+    __nv_bfloat16 *Aq, *Bq;  // [2 KSh][S][R8 x KSTEP], [2 KSh][S][64 x KSTEP]
+};
+
+__global__ void k_gram_split_A(GramSplitArgs a) {
+    const int tile = a.R8 * KSTEP;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)a.KSh * tile) return;
+    const int e = (int)(g % tile);
+    const int ksr = (int)(g / tile);
+    int rl, kl;
+    tile_pos(e, rl, kl);
+    const int64_t kx = (int64_t)ksr * KSTEP + kl;
+    __nv_bfloat16 re[S], im[S];
+    if (rl < a.m && kx < a.nrow && isfinite(a.colmax[rl])) {
+        const double2 v = a.A[(int64_t)rl * a.cs + a.r0 + kx];
+        const int k = 49 - exponent_of(a.colmax[rl]);
+        digits7(fixed_of(v.x, k), re);
+        digits7(fixed_of(v.y, k), im);
+    } else {
+        for (int p = 0; p < S; p++) re[p] = im[p] = __double2bfloat16(0.0);
+    }
+    const int64_t bre = (int64_t)ksr * S, bim = (int64_t)(a.KSh + ksr) * S;
+    for (int p = 0; p < S; p++) {
+        a.Aq[(bre + p) * tile + e] = re[p];
+        a.Aq[(bim + p) * tile + e] = im[p];
+    }
+}
+
+__global__ void k_gram_split_B(GramSplitArgs a) {
+    const int tile = TN * KSTEP;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)a.KSh * tile) return;
+    const int e = (int)(g % tile);
+    const int ksr = (int)(g / tile);
+    int col, kl;
+    tile_pos(e, col, kl);
+    const int64_t kx = (int64_t)ksr * KSTEP + kl;
+    const int j = col < a.m ? col : col - a.m;
+    __nv_bfloat16 lo[S], hi[S];
+    if (col < 2 * a.m && kx < a.nrow && isfinite(a.colmax[j])) {
+        const double2 v = a.A[(int64_t)j * a.cs + a.r0 + kx];
+        const int k = 49 - exponent_of(a.colmax[j]);
+        digits7(fixed_of(col < a.m ? v.x : v.y, k), lo);
+        digits7(fixed_of(col < a.m ? v.y : -v.x, k), hi);
+    } else {
+        for (int p = 0; p < S; p++) lo[p] = hi[p] = __double2bfloat16(0.0);
+    }
+    const int64_t blo = (int64_t)ksr * S, bhi = (int64_t)(a.KSh + ksr) * S;
+    for (int p = 0; p < S; p++) {
+        a.Bq[(blo + p) * tile + e] = lo[p];
+        a.Bq[(bhi + p) * tile + e] = hi[p];
+    }
+}
+
+// G[i][j] = 2^(e_i + e_j - 14) (sum of the K-range partials of the real and the
+// imaginary column), fixed order.
+__global__ void k_gram_finish(const double *part, int ksplit, int m, const double *colmax, double2 *G) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= m * m) return;
+    const int i = g / m, j = g % m;
+    double re = 0, im = 0;
+    for (int s = 0; s < ksplit; s++) {
+        const double *p = part + ((int64_t)s * TM + i) * TN;
+        re += p[j];
+        im += p[m + j];
+    }
+    const int sc = exponent_of(colmax[i]) + exponent_of(colmax[j]) - 14;
+    double2 v = make_double2(ldexp(re, sc), ldexp(im, sc));
+    if (!isfinite(colmax[i]) || !isfinite(colmax[j])) v = make_double2(NAN, NAN);
+    G[g] = v;
+}
+
+}  // namespace
+
+namespace ddp {
+
+// Gram blocks of nseg consecutive row segments of seg rows each on the tensor cores:
+// out[z][i][j] = sum over the rows r of segment z of conj(A_i[r]) A_j[r], A_i[r] the
+// complex component r of column i (column stride cs); A and out on the device, m <= 32.
+int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int nseg, double2 *out) {
+    if (m < 1 || 2 * m > TN) return DDP_ERR_UNSUPPORTED;
+    const int R8 = 8 * ((m + 7) / 8);
+    const int a_bytes = R8 * KSTEP * 2;
+    const int64_t KSh64 = (seg + KSTEP - 1) / KSTEP;
+    if (KSh64 > (1 << 28)) return DDP_ERR_UNSUPPORTED;
+    const int KSh = (int)KSh64, KS = 2 * KSh;
+    int ksplit = std::max(1, std::min(KS, 152));
+    ksplit = std::max(ksplit, (KS + MAX_STEPS_PER_BLOCK - 1) / MAX_STEPS_PER_BLOCK);
+    const size_t bA = (size_t)S * KS * a_bytes, bB = (size_t)S * KS * TILE_B;
+    const size_t bP = (size_t)ksplit * TM * TN * sizeof(double);
+    Arena &ar = ctx->aux;
+    ar.reset();
+    DDP_CUDA(ctx, ar.reserve(bA + bB + bP + (size_t)m * 8 + 64 + 6 * 256));
+    uint8_t *Aq = (uint8_t *)ar.take(bA);
+    uint8_t *Bq = (uint8_t *)ar.take(bB);
+    double *part = (double *)ar.take(bP);
+    double *colmax = (double *)ar.take((size_t)m * 8);
+    int *err = (int *)ar.take(64);
+    const size_t gsm = (size_t)NSTAGE * STAGE;
+    DDP_CUDA(ctx, cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    cudaStream_t st = ctx->stream;
+    DDP_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
+    for (int z = 0; z < nseg; z++) {
+        DDP_CUDA(ctx, cudaMemsetAsync(colmax, 0, (size_t)m * 8, st));
+        const int64_t r0 = (int64_t)z * seg;
+        k_gram_max<<<dim3((unsigned)std::min<int64_t>(64, (seg + 255) / 256), m), 256, 0, st>>>(A, cs, m, r0, seg,
+                                                                                            colmax);
+        GramSplitArgs sa;
+        sa.A = A;
+        sa.cs = cs;
+        sa.r0 = r0;
+        sa.nrow = seg;
+        sa.m = m;
+        sa.R8 = R8;
+        sa.KSh = KSh;
+        sa.colmax = colmax;
+        sa.Aq = (__nv_bfloat16 *)Aq;
+        sa.Bq = (__nv_bfloat16 *)Bq;
+        const int64_t na = (int64_t)KSh * R8 * KSTEP, nb = (int64_t)KSh * TN * KSTEP;
+        k_gram_split_A<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(sa);
+        k_gram_split_B<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(sa);
+        GemmArgs g;
+        g.Aq = Aq;
+        g.Bq = Bq;
+        g.a_bytes = a_bytes;
+        g.MT = 1;
+        g.NT = 1;
+        g.KS = KS;
+        g.ksplit = ksplit;
+        g.ncols = TN;
+        g.part = part;
+        g.err = err;
+        k_ozaki_gemm<<<dim3(1, 1, ksplit), GEMM_BLOCK, gsm, st>>>(g);
+        k_gram_finish<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(part, ksplit, m, colmax,
+                                                                       out + (int64_t)z * m * m);
+        ctx->launches += 5;
+        DDP_CUDA(ctx, cudaGetLastError());
+    }
+    int h = 0;
+    DDP_CUDA(ctx, cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DDP_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h) {
+        snprintf(ctx->last_error, sizeof(ctx->last_error), "Gram blocks: a wait for the tensor cores gave up");
         return DDP_ERR_CUDA;
     }
     return DDP_OK;

@@ -23,6 +23,12 @@ GSTAR = ((6, 0, 0, 0), (5, 4, 4, 4))   # slices 6..10
 OMEGA = ((4, 0, 0, 0), (4, 4, 4, 4))   # slices 4..7
 VOL3 = L[1] * L[2] * L[3]
 CORR_TOL = 1e-7
+# Tensor-core path: every term of a slice sum is exact to ~2^-47 of its row maximum
+# times its column maximum (seven 7-bit slices per operand, exact integer
+# accumulation), so on random fields the norm-wise error stays near 1e-14; the
+# bound 1e-12 leaves the factor ~40 of max/rms of the two operands.  The direct
+# FP64 kernel rounds only in FP64.
+TC_TOL = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -55,52 +61,66 @@ def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def test_orthonormalize_matches_oracle(ddp, env):
+class _Path:
+    """Selects the tensor-core (1) or the direct FP64 (0) projector-cut kernels for a block."""
+
+    def __init__(self, ddp, ctx, tc):
+        self.ddp, self.ctx, self.tc = ddp, ctx, tc
+
+    def __enter__(self):
+        self.ddp.ddp_set_param(self.ctx, "projector_tensor_cores", self.tc)
+
+    def __exit__(self, *exc):
+        self.ddp.ddp_set_param(self.ctx, "projector_tensor_cores", 1)
+
+
+@pytest.mark.parametrize("tc", [1, 0])
+def test_orthonormalize_matches_oracle(ddp, env, tc):
     U, ctx, doms = env
     n = oracle.box_sites(OMEGA[1])
     V = synth.random_spinor(8, n, 3)
     Vd = _dev(V)
-    ddp.ddp_orthonormalize(ctx, doms["omega"], Vd, 8)
+    with _Path(ddp, ctx, tc):
+        ddp.ddp_orthonormalize(ctx, doms["omega"], Vd, 8)
     assert np.abs(Vd.cpu().numpy() - projector.orthonormalize(V)).max() < 1e-12
 
 
+@pytest.mark.parametrize("tc", [1, 0])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_inverse_iteration_matches_oracle(ddp, env, prec):
+def test_inverse_iteration_matches_oracle(ddp, env, prec, tc):
     U, ctx, doms = env
     n = oracle.box_sites(OMEGA[1])
     V0 = synth.random_spinor(6, n, 7)
     want = projector.inverse_iteration(U, L, AP, *OMEGA, KAPPA, V0, 3)
     Vd = _dev(V0)
-    rc, _ = ddp.ddp_inverse_iteration(ctx, doms["omega"], KAPPA, Vd, 6, 3, 1e-11, prec)
+    with _Path(ddp, ctx, tc):
+        rc, _ = ddp.ddp_inverse_iteration(ctx, doms["omega"], KAPPA, Vd, 6, 3, 1e-11, prec)
     assert rc == ddp.DDP_OK
     got = Vd.cpu().numpy()
     assert max(_rel(got[c], want[c]) for c in range(6)) < 1e-8
 
 
-def test_gram_slices_matches_oracle(ddp, env):
+@pytest.mark.parametrize("tc", [1, 0])
+def test_gram_slices_matches_oracle(ddp, env, tc):
     U, ctx, doms = env
     n = oracle.box_sites(GBAR[1])
     A = synth.random_spinor(20, n, 11)
     M = torch.zeros((L[0], 20, 20), dtype=torch.complex128, device="cuda")
-    ddp.ddp_gram_slices(ctx, doms["bar"], _dev(A), 20, M)
+    with _Path(ddp, ctx, tc):
+        ddp.ddp_gram_slices(ctx, doms["bar"], _dev(A), 20, M)
     want = projector.gram_slices(L, *GBAR, A)
-    assert _rel(M.cpu().numpy(), want) < 1e-13
+    assert _rel(M.cpu().numpy(), want) < (TC_TOL if tc else 1e-13)
     # a domain that wraps in time puts its slices at their global times (host buffers)
     wrap = ((10, 1, 0, 0), (4, 2, 4, 4))
     did = ddp.ddp_set_domain(ctx, doms["gid"], *wrap)
     M2 = np.zeros((L[0], 20, 20), dtype=np.complex128)
     A2 = synth.random_spinor(20, oracle.box_sites(wrap[1]), 12)
-    ddp.ddp_gram_slices(ctx, did, A2, 20, M2)
-    assert _rel(M2, projector.gram_slices(L, *wrap, A2)) < 1e-13
+    with _Path(ddp, ctx, tc):
+        ddp.ddp_gram_slices(ctx, did, A2, 20, M2)
+    assert _rel(M2, projector.gram_slices(L, *wrap, A2)) < (TC_TOL if tc else 1e-13)
     ddp.ddp_free_domain(ctx, did)
 
 
-# Tensor-core path: every term of a slice sum is exact to ~2^-47 of its row maximum
-# times its column maximum (seven 7-bit slices per operand, exact integer
-# accumulation), so on random fields the norm-wise error stays near 1e-14; the
-# bound 1e-12 leaves the factor ~40 of max/rms of the two operands.  The direct
-# FP64 kernel rounds only in FP64.
-TC_TOL = 1e-12
 
 
 def _forms(A, form):
@@ -115,11 +135,11 @@ def test_colourless_slices_matches_oracle(ddp, env, form, tc):
     n = oracle.box_sites(GSTAR[1])
     A = synth.random_spinor(5, n, 13)
     X = torch.zeros((L[0], 5, 5, 5, 4), dtype=torch.complex128, device="cuda")
-    ddp.ddp_set_param(ctx, "colour_tensor_cores", tc)
+    ddp.ddp_set_param(ctx, "projector_tensor_cores", tc)
     try:
         ddp.ddp_colourless_slices(ctx, doms["star"], _dev(A), 5, form, X)
     finally:
-        ddp.ddp_set_param(ctx, "colour_tensor_cores", 1)
+        ddp.ddp_set_param(ctx, "projector_tensor_cores", 1)
     want = projector.colourless_spinors(L, *GSTAR, _forms(A, form))
     assert _rel(X.cpu().numpy(), want) < (TC_TOL if tc else 1e-13)
 
@@ -143,11 +163,11 @@ def _colourless_both(ddp, ctx, did, A, m, form, L0):
     out = []
     for tc in (1, 0):
         X = torch.zeros((L0, m, m, m, 4), dtype=torch.complex128, device="cuda")
-        ddp.ddp_set_param(ctx, "colour_tensor_cores", tc)
+        ddp.ddp_set_param(ctx, "projector_tensor_cores", tc)
         try:
             ddp.ddp_colourless_slices(ctx, did, _dev(A), m, form, X)
         finally:
-            ddp.ddp_set_param(ctx, "colour_tensor_cores", 1)
+            ddp.ddp_set_param(ctx, "projector_tensor_cores", 1)
         out.append(X.cpu().numpy())
     return out
 
@@ -280,11 +300,11 @@ def test_colourless_nan_input_stays_local(ddp, env8, tc):
     A = synth.random_spinor(m, oracle.box_sites(box[1]), 78)
     A[bad, 700, 1, 2] = np.nan            # site 700 lies in the second time slice
     X = torch.zeros((L8[0], m, m, m, 4), dtype=torch.complex128, device="cuda")
-    ddp.ddp_set_param(ctx, "colour_tensor_cores", tc)
+    ddp.ddp_set_param(ctx, "projector_tensor_cores", tc)
     try:
         ddp.ddp_colourless_slices(ctx, did, _dev(A), m, 0, X)
     finally:
-        ddp.ddp_set_param(ctx, "colour_tensor_cores", 1)
+        ddp.ddp_set_param(ctx, "projector_tensor_cores", 1)
         ddp.ddp_free_domain(ctx, did)
     X = X.cpu().numpy()
     clean = A.copy()
@@ -299,3 +319,70 @@ def test_colourless_nan_input_stays_local(ddp, env8, tc):
     assert np.isfinite(X[1][~involved]).all() and np.isfinite(X[0]).all()
     assert _rel(X[1][~involved], want[1][~involved]) < TC_TOL
     assert _rel(X[0], want[0]) < TC_TOL
+
+
+@pytest.mark.parametrize("m,box", [(1, ((0, 0, 0, 0), (3, 8, 8, 8))),
+                                   (20, ((1, 0, 0, 0), (2, 8, 8, 8))),
+                                   (32, ((4, 0, 0, 0), (3, 8, 8, 8)))])
+def test_gram_tensor_cores_sizes(ddp, env8, m, box):
+    """m = 1, 20 and 32 (the largest) columns over 512-site slices, the last box wrapping
+    in time; both paths against the oracle, slices outside the box zero."""
+    ctx, gid = env8
+    did = ddp.ddp_set_domain(ctx, gid, *box)
+    A = synth.random_spinor(m, oracle.box_sites(box[1]), 60 + m)
+    want = projector.gram_slices(L8, *box, A)
+    out = {}
+    for tc in (1, 0):
+        M = torch.zeros((L8[0], m, m), dtype=torch.complex128, device="cuda")
+        with _Path(ddp, ctx, tc):
+            ddp.ddp_gram_slices(ctx, did, _dev(A), m, M)
+        out[tc] = M.cpu().numpy()
+    ddp.ddp_free_domain(ctx, did)
+    assert _rel(out[0], want) < 1e-13
+    assert _rel(out[1], want) < TC_TOL
+    inside = np.zeros(L8[0], bool)
+    inside[[(box[0][0] + t) % L8[0] for t in range(box[1][0])]] = True
+    assert not np.any(out[1][~inside])
+
+
+def test_gram_tensor_cores_wide_dynamic_range(ddp, env8):
+    """Columns scaled from 1e-30 to 1e6: every entry is accurate relative to the norms of
+    its two columns (each column carries its own exponent)."""
+    ctx, gid = env8
+    box = ((0, 0, 0, 0), (2, 8, 8, 8))
+    did = ddp.ddp_set_domain(ctx, gid, *box)
+    m = 8
+    A = synth.random_spinor(m, oracle.box_sites(box[1]), 79) * (10.0 ** np.linspace(-30, 6, m))[:, None, None, None]
+    M = torch.zeros((L8[0], m, m), dtype=torch.complex128, device="cuda")
+    ddp.ddp_gram_slices(ctx, did, _dev(A), m, M)
+    ddp.ddp_free_domain(ctx, did)
+    got, want = M.cpu().numpy(), projector.gram_slices(L8, *box, A)
+    for t in range(2):
+        nrm = np.sqrt(np.abs(np.diagonal(want[t])))
+        assert np.all(np.abs(got[t] - want[t]) <= TC_TOL * np.outer(nrm, nrm))
+
+
+@pytest.mark.parametrize("tc", [1, 0])
+def test_gram_nan_input_stays_local(ddp, env8, tc):
+    """A NaN in one column at one site makes that slice's row and column of the Gram block
+    NaN and nothing else."""
+    ctx, gid = env8
+    box = ((0, 0, 0, 0), (2, 8, 8, 8))
+    did = ddp.ddp_set_domain(ctx, gid, *box)
+    m, bad = 5, 3
+    A = synth.random_spinor(m, oracle.box_sites(box[1]), 80)
+    A[bad, 900, 2, 1] = np.nan            # the second time slice
+    M = torch.zeros((L8[0], m, m), dtype=torch.complex128, device="cuda")
+    with _Path(ddp, ctx, tc):
+        ddp.ddp_gram_slices(ctx, did, _dev(A), m, M)
+    ddp.ddp_free_domain(ctx, did)
+    got = M.cpu().numpy()
+    clean = A.copy()
+    clean[bad, 900, 2, 1] = 0
+    want = projector.gram_slices(L8, *box, clean)
+    involved = np.zeros((m, m), bool)
+    involved[bad] = involved[:, bad] = True
+    assert np.isnan(got[1][involved]).all()
+    assert np.isfinite(got[1][~involved]).all() and np.isfinite(got[0]).all()
+    assert _rel(got[1][~involved], want[1][~involved]) < TC_TOL
+    assert _rel(got[0], want[0]) < TC_TOL
