@@ -63,23 +63,75 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def _stencil_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ddp_device.cuh", "ddp_kernels.cuh", "clover.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1601_04587_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def hop_traffic_record():
     """ncu DRAM bytes per launch of the stencil kernel, if the committed record
     matches the current kernel sources."""
-    import hashlib
     p = os.path.join(ROOT, "profiles", "hop_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         rec = json.load(open(p))
-        h = hashlib.sha256()
-        for f in ("ddp_device.cuh", "ddp_kernels.cuh", "clover.cuh"):
-            h.update(open(os.path.join(ROOT, "paper_1601_04587_gb300", "csrc", f), "rb").read())
-        if rec.get("sources_sha256") != h.hexdigest():
+        if rec.get("sources_sha256") != _stencil_sources_sha256():
             return None
         return rec
     except Exception:
         return None
+
+
+HOP_TRAFFIC_LATTICE = (32, 24, 24, 24)
+HOP_TRAFFIC_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,"
+                       "l1tex__m_xbar2l1tex_read_bytes.sum,launch__registers_per_thread")
+
+
+def write_hop_traffic(csv_path):
+    """profiles/hop_traffic.json from the ncu CSV of the three FP32 stencils on the
+    32x24^3 lattice (the --workload hop run with --iters 1 under
+    `ncu --metrics HOP_TRAFFIC_METRICS --clock-control none -k regex:k_hop --csv`):
+    DRAM bytes per launch, scaled by site-columns to the 48x24^3 bench launch."""
+    import csv
+    rows = [r for r in csv.reader(open(csv_path)) if r]
+    hdr = next(r for r in rows if "Kernel Name" in r and "Metric Name" in r)
+    ix = {k: hdr.index(k) for k in ("Kernel Name", "Metric Name", "Metric Value", "ID")}
+    per = {}
+    for r in rows[rows.index(hdr) + 1:]:
+        if len(r) != len(hdr) or "k_hop" not in r[ix["Kernel Name"]]:
+            continue
+        d = per.setdefault(r[ix["ID"]], {"name": r[ix["Kernel Name"]]})
+        d[r[ix["Metric Name"]]] = float(r[ix["Metric Value"]].replace(",", ""))
+    names = {"k_hop<PF32, 0, 0,": "fp32/plain", "k_hop<PF32, 1, 1,": "fp32/schur_rhat", "k_hop<PF32, 1, 2,": "fp32/schur_ts"}
+    captured = {}
+    for d in per.values():
+        key = next((v for k, v in names.items() if k in d["name"].replace("ddp::", "")), None)
+        if key is not None and "dram__bytes_read.sum" in d:
+            b = d["dram__bytes_read.sum"] + d["dram__bytes_write.sum"]
+            captured[key] = min(captured.get(key, b), b)  # launches after the first: warm L2
+    sites = HOP_TRAFFIC_LATTICE[0] * HOP_TRAFFIC_LATTICE[1] * HOP_TRAFFIC_LATTICE[2] * HOP_TRAFFIC_LATTICE[3] // 2
+    per_site_col = {"fp32/plain": 224, "fp32/schur_rhat": 416, "fp32/schur_ts": 320}
+    scale = 48 / HOP_TRAFFIC_LATTICE[0]
+    rec = {"what": "ncu DRAM bytes (read + write) per launch of the three inner-loop stencils, FP32 storage, 12 columns",
+           "captured_lattice": list(HOP_TRAFFIC_LATTICE), "ncol": 12,
+           "captured_bytes": captured,
+           "captured_algorithmic_bytes": {k: per_site_col[k] * sites * 12 for k in captured},
+           "scale_to_bench": scale,
+           "note": "the 48x24^3 launch has 1.5x the captured site-columns; DRAM traffic of these kernels scales with "
+                   "site-columns (their re-reads are neighbour gathers missing L2), so the bench's per-launch traffic "
+                   "is the captured bytes x 1.5",
+           "kernels": {k: v * scale for k, v in captured.items()},
+           "command": "python bench.py --workload hop --lattice 32 24 24 24 --precision fp32 --kernel "
+                      "plain,schur_rhat,schur_ts --iters 1 (under ncu --metrics " + HOP_TRAFFIC_METRICS +
+                      " --clock-control none -k regex:k_hop --csv), then python bench.py --write-hop-traffic CSV",
+           "sources_sha256": _stencil_sources_sha256()}
+    with open(os.path.join(ROOT, "profiles", "hop_traffic.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
 
 
 class ClockSampler:
@@ -569,7 +621,12 @@ def main():
     ap.add_argument("--csw", type=float, default=0.0, help="slabs: clover coefficient c_sw (default 0)")
     ap.add_argument("--no-conditional", action="store_true",
                     help="run the inner loop as host-polled graph chunks (profilers see its kernels)")
+    ap.add_argument("--write-hop-traffic", metavar="CSV", default=None,
+                    help="write profiles/hop_traffic.json from an ncu CSV of the stencil bytes and exit")
     args = ap.parse_args()
+    if args.write_hop_traffic:
+        write_hop_traffic(args.write_hop_traffic)
+        return
     global KAPPA, CSW
     if args.kappa is not None:
         KAPPA = args.kappa

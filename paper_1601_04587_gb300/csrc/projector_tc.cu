@@ -107,6 +107,14 @@ __device__ __forceinline__ int exponent_of(double mx) {
     return e;
 }
 
+// The shared exponent of every row or column: e with max < 2^e, or NONFINITE for a
+// row or column that holds a NaN or an infinity (its slices are zero and its outputs NaN).
+constexpr int NONFINITE = -100000;
+__global__ void k_exponents(const double *mx, int n, int *ex) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) ex[i] = isfinite(mx[i]) ? exponent_of(mx[i]) : NONFINITE;
+}
+
 // (i, j), i <= j, of the symmetric row r (rows ordered i-major).
 __device__ __forceinline__ void pair_of(int r, int m, int &i, int &j) {
     i = 0;
@@ -347,7 +355,7 @@ struct SplitArgs {
     int64_t n, site0, K;  // K = 3 slice_n
     int m, form, rows;
     int MT, NT, KSh;      // tiles; K steps of one half (Re / Im) of the reduction
-    const double *rowmax, *colmax;
+    const int *rexp, *cexp;  // exponents of the rows of A' and of the spinor columns (k, alpha)
     __nv_bfloat16 *Aq, *Bq;  // [MT][2 KSh][S][128 x KSTEP], [NT][2 KSh][S][64 x KSTEP]
 };
 
@@ -365,9 +373,10 @@ __global__ void k_split_A(SplitArgs a) {
     const int r = mt * TM + rl;
     const int64_t kx = (int64_t)ksr * KSTEP + kl;
     __nv_bfloat16 re[S], im[S];
-    if (r < a.rows && kx < a.K && isfinite(a.rowmax[r])) {
+    const int er = r < a.rows ? a.rexp[r] : NONFINITE;
+    if (kx < a.K && er != NONFINITE) {
         const float4 v = a.E[(int64_t)r * a.K + kx];
-        const int k = 49 - exponent_of(a.rowmax[r]);
+        const int k = 49 - er;
         digits7(fixed_of(v.x, k) + fixed_of(v.y, k), re);
         digits7(fixed_of(v.z, k) + fixed_of(v.w, k), im);
     } else {
@@ -397,12 +406,13 @@ __global__ void k_split_B(SplitArgs a) {
     const int Q = 4 * a.m;
     const int q = col < Q ? col : col - Q;
     __nv_bfloat16 lo[S], hi[S];
-    if (col < 2 * Q && kx < a.K && isfinite(a.colmax[q])) {
+    const int eq = col < 2 * Q ? a.cexp[q] : NONFINITE;
+    if (kx < a.K && eq != NONFINITE) {
         const int k = q / 4, al = q % 4;
         const int64_t x = kx / 3;
         const int c = (int)(kx % 3);
         const double2 v = form_of(a.A[((int64_t)k * a.n + a.site0 + x) * 12 + 3 * al + c], a.form, al);
-        const int sc = 49 - exponent_of(a.colmax[q]);
+        const int sc = 49 - eq;
         digits7(fixed_of(col < Q ? v.x : v.y, sc), lo);
         digits7(fixed_of(col < Q ? -v.y : v.x, sc), hi);
     } else {
@@ -661,13 +671,15 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
     const size_t bP = (size_t)ksplit * prow * ncols * sizeof(double);
     Arena &ar = ctx->aux;
     ar.reset();
-    DDP_CUDA(ctx, ar.reserve(bE + bA + bB + bP + (size_t)(rows + Q) * 8 + 64 + 8 * 256));
+    DDP_CUDA(ctx, ar.reserve(bE + bA + bB + bP + (size_t)(rows + Q) * 12 + 64 + 10 * 256));
     float4 *E = (float4 *)ar.take(bE);
     uint8_t *Aq = (uint8_t *)ar.take(bA);
     uint8_t *Bq = (uint8_t *)ar.take(bB);
     double *part = (double *)ar.take(bP);
     double *rowmax = (double *)ar.take((size_t)rows * 8);
     double *colmax = (double *)ar.take((size_t)Q * 8);
+    int *rexp = (int *)ar.take((size_t)rows * 4);
+    int *cexp = (int *)ar.take((size_t)Q * 4);
     int *err = (int *)ar.take(64);
     const size_t esm = (size_t)m * ESITES * 12 * sizeof(float4);
     const size_t gsm = (size_t)NSTAGE * STAGE;
@@ -705,8 +717,10 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
         sa.MT = MT;
         sa.NT = NT;
         sa.KSh = KSh;
-        sa.rowmax = rowmax;
-        sa.colmax = colmax;
+        k_exponents<<<(rows + 255) / 256, 256, 0, st>>>(rowmax, rows, rexp);
+        k_exponents<<<(Q + 255) / 256, 256, 0, st>>>(colmax, Q, cexp);
+        sa.rexp = rexp;
+        sa.cexp = cexp;
         sa.Aq = (__nv_bfloat16 *)Aq;
         sa.Bq = (__nv_bfloat16 *)Bq;
         const int64_t na = (int64_t)MT * KSh * TM * KSTEP, nb = (int64_t)NT * KSh * TN * KSTEP;
@@ -727,7 +741,7 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
         const int64_t nx = (int64_t)rows * Q;
         k_ozaki_finish<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(
             part, ksplit, prow, ncols, m, rows, rowmax, colmax, X + (int64_t)((o0 + z) % L0) * m * m * Q);
-        ctx->launches += 6;
+        ctx->launches += 8;
         DDP_CUDA(ctx, cudaGetLastError());
     }
     int h = 0;
@@ -771,7 +785,7 @@ struct GramSplitArgs {
     const double2 *A;
     int64_t cs, r0, nrow;  // column stride; the segment's rows
     int m, R8, KSh;
-    const double *colmax;
+    const int *cexp;       // exponents of the columns
     __nv_bfloat16 *Aq, *Bq;  // [2 KSh][S][R8 x KSTEP], [2 KSh][S][64 x KSTEP]
 };
 
@@ -785,9 +799,10 @@ __global__ void k_gram_split_A(GramSplitArgs a) {
     tile_pos(e, rl, kl);
     const int64_t kx = (int64_t)ksr * KSTEP + kl;
     __nv_bfloat16 re[S], im[S];
-    if (rl < a.m && kx < a.nrow && isfinite(a.colmax[rl])) {
+    const int er = rl < a.m ? a.cexp[rl] : NONFINITE;
+    if (kx < a.nrow && er != NONFINITE) {
         const double2 v = a.A[(int64_t)rl * a.cs + a.r0 + kx];
-        const int k = 49 - exponent_of(a.colmax[rl]);
+        const int k = 49 - er;
         digits7(fixed_of(v.x, k), re);
         digits7(fixed_of(v.y, k), im);
     } else {
@@ -811,9 +826,10 @@ __global__ void k_gram_split_B(GramSplitArgs a) {
     const int64_t kx = (int64_t)ksr * KSTEP + kl;
     const int j = col < a.m ? col : col - a.m;
     __nv_bfloat16 lo[S], hi[S];
-    if (col < 2 * a.m && kx < a.nrow && isfinite(a.colmax[j])) {
+    const int ej = col < 2 * a.m ? a.cexp[j] : NONFINITE;
+    if (kx < a.nrow && ej != NONFINITE) {
         const double2 v = a.A[(int64_t)j * a.cs + a.r0 + kx];
-        const int k = 49 - exponent_of(a.colmax[j]);
+        const int k = 49 - ej;
         digits7(fixed_of(col < a.m ? v.x : v.y, k), lo);
         digits7(fixed_of(col < a.m ? v.y : -v.x, k), hi);
     } else {
@@ -864,11 +880,12 @@ int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int 
     const size_t bP = (size_t)ksplit * TM * TN * sizeof(double);
     Arena &ar = ctx->aux;
     ar.reset();
-    DDP_CUDA(ctx, ar.reserve(bA + bB + bP + (size_t)m * 8 + 64 + 6 * 256));
+    DDP_CUDA(ctx, ar.reserve(bA + bB + bP + (size_t)m * 12 + 64 + 7 * 256));
     uint8_t *Aq = (uint8_t *)ar.take(bA);
     uint8_t *Bq = (uint8_t *)ar.take(bB);
     double *part = (double *)ar.take(bP);
     double *colmax = (double *)ar.take((size_t)m * 8);
+    int *cexp = (int *)ar.take((size_t)m * 4);
     int *err = (int *)ar.take(64);
     const size_t gsm = (size_t)NSTAGE * STAGE;
     DDP_CUDA(ctx, cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
@@ -887,7 +904,8 @@ int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int 
         sa.m = m;
         sa.R8 = R8;
         sa.KSh = KSh;
-        sa.colmax = colmax;
+        k_exponents<<<(m + 255) / 256, 256, 0, st>>>(colmax, m, cexp);
+        sa.cexp = cexp;
         sa.Aq = (__nv_bfloat16 *)Aq;
         sa.Bq = (__nv_bfloat16 *)Bq;
         const int64_t na = (int64_t)KSh * R8 * KSTEP, nb = (int64_t)KSh * TN * KSTEP;
@@ -907,7 +925,7 @@ int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int 
         k_ozaki_gemm<<<dim3(1, 1, ksplit), GEMM_BLOCK, gsm, st>>>(g);
         k_gram_finish<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(part, ksplit, m, colmax,
                                                                        out + (int64_t)z * m * m);
-        ctx->launches += 5;
+        ctx->launches += 6;
         DDP_CUDA(ctx, cudaGetLastError());
     }
     int h = 0;
