@@ -1062,7 +1062,19 @@ int ddp_propagator_series(ddp_ctx *ctx, int n, const int *domain_ids, double kap
         r.tol = tol;
         r.out = dS[i];
     }
-    int worst = run_solves(ctx, reqs.data(), n, precision, infos);
+    // With host outputs the smaller nested domains are solved first and their
+    // propagators and series terms are copied to the host while the largest domain
+    // solves; with device outputs all domains share one batched solve.  A domain's
+    // result does not depend on the batch it is solved in.
+    bool host_out = false;
+    for (int i = 0; i < n; i++) host_out = host_out || s_host[i] || t_host[i];
+    const int first = (host_out && n > 1) ? n - 1 : n;
+    auto combine = [](int a, int b) {
+        if (a != DDP_OK && a != DDP_ERR_NOT_CONVERGED) return a;
+        if (b != DDP_OK && b != DDP_ERR_NOT_CONVERGED) return b;
+        return (a == DDP_ERR_NOT_CONVERGED || b == DDP_ERR_NOT_CONVERGED) ? (int)DDP_ERR_NOT_CONVERGED : (int)DDP_OK;
+    };
+    int worst = run_solves(ctx, reqs.data(), first, precision, infos);
     if (worst != DDP_OK && worst != DDP_ERR_NOT_CONVERGED) return worst;
     if (!ctx->copy_stream) DDP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
     cudaStream_t cs = ctx->copy_stream;
@@ -1074,11 +1086,9 @@ int ddp_propagator_series(ddp_ctx *ctx, int n, const int *domain_ids, double kap
         DDP_CUDA(ctx, cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyDeviceToHost, cs));
         return DDP_OK;
     };
-    int rc = DDP_OK;
-    for (int i = 0; i < n && !rc; i++)
-        if (s_host[i]) rc = download(S_out[i], dS[i], sb[i]);
-    for (int i = 1; i < n && !rc; i++) {
-        if (!dT[i]) continue;
+    // series term T_i = S_i - E S_{i-1} on the device, then its copy to the host
+    auto series = [&](int i) -> int {
+        if (!dT[i]) return DDP_OK;
         SeriesArgs sa;
         sa.big = item_of(g, *dom[i], 12, DDP_PREC_FP64);
         sa.small = item_of(g, *dom[i - 1], 12, DDP_PREC_FP64);
@@ -1089,11 +1099,20 @@ int ddp_propagator_series(ddp_ctx *ctx, int n, const int *domain_ids, double kap
         const int64_t nt = (int64_t)12 * dom[i]->n;
         k_series<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(sa);
         ctx->launches++;
-        if (cudaPeekAtLastError() != cudaSuccess) {
-            rc = set_cuda_error(ctx, cudaGetLastError(), "series term");
-            break;
-        }
-        if (t_host[i]) rc = download(T_out[i - 1], dT[i], sb[i]);
+        if (cudaPeekAtLastError() != cudaSuccess) return set_cuda_error(ctx, cudaGetLastError(), "series term");
+        return t_host[i] ? download(T_out[i - 1], dT[i], sb[i]) : DDP_OK;
+    };
+    int rc = DDP_OK;
+    for (int i = 0; i < first && !rc; i++)
+        if (s_host[i]) rc = download(S_out[i], dS[i], sb[i]);
+    for (int i = 1; i < first && !rc; i++) rc = series(i);
+    if (!rc && first < n) {
+        const int w = run_solves(ctx, reqs.data() + first, n - first, precision, infos ? infos + first : nullptr);
+        if (w != DDP_OK && w != DDP_ERR_NOT_CONVERGED) rc = w;
+        worst = combine(worst, w);
+        for (int i = first; i < n && !rc; i++)
+            if (s_host[i]) rc = download(S_out[i], dS[i], sb[i]);
+        for (int i = first; i < n && !rc; i++) rc = series(i);
     }
     for (int i = 0; i < n && !rc && contract_mask; i++)
         for (int k = 0; k < 4 && !rc; k++) {
