@@ -303,7 +303,9 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * "tile_cols" (columns per block, 1..12, 0 = automatic), "tuned_cols_fp64" ...
  * "tuned_cols_bf16" (a remembered autotuner choice, 0 = none), "conditional" (1: the
  * inner loop is a device-driven CUDA-graph WHILE node; 0: host-polled graph
- * chunks), "projector_tensor_cores" (1, the default: the Gram blocks and colourless
+ * chunks), "stencil_carveout" (preferred shared-memory share of the unified L1 /
+ * shared memory for the inner-loop stencils, percent; default 28, -1 = the driver's
+ * choice), "projector_tensor_cores" (1, the default: the Gram blocks and colourless
  * spinor sums of the projector cut, m <= 32, run as an emulated-FP64 product on the
  * tensor cores; 0: direct FP64 kernels).  DDP_ERR_INVALID_ARG for unknown names or
  * values. */

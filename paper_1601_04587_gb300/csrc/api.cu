@@ -1159,7 +1159,7 @@ int ddp_boundary_source(ddp_ctx *ctx, int domain_from, const double *psi, int do
 }
 
 // Tuning knobs of the solver (names: max_outer, max_inner, delta_fp32,
-// delta_fp16, delta_bf16, delta_fp64, tile_sites, tile_cols, conditional, projector_tensor_cores).
+// delta_fp16, delta_bf16, delta_fp64, tile_sites, tile_cols, conditional, stencil_carveout, projector_tensor_cores).
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
     if (!ctx || !name) return DDP_ERR_INVALID_ARG;
     EngineParams &p = ctx->prm;
@@ -1177,6 +1177,10 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
         p.CG = (int)value;
     } else if (n == "conditional") p.use_conditional = value != 0;
     else if (n == "projector_tensor_cores") p.proj_tc = value != 0;
+    else if (n == "stencil_carveout") {
+        if (value < -1 || value > 100) return DDP_ERR_INVALID_ARG;
+        p.carveout = (int)value;
+    }
     else if (n == "tuned_cols_fp64" || n == "tuned_cols_fp32" || n == "tuned_cols_fp16" || n == "tuned_cols_bf16") {
         if (value < 0 || value > HOP_MAX_CG) return DDP_ERR_INVALID_ARG;
         int k = n == "tuned_cols_fp64" ? 0 : n == "tuned_cols_fp32" ? 1 : n == "tuned_cols_fp16" ? 2 : 3;

@@ -80,6 +80,10 @@ struct EngineParams {
     int CG_prec[4] = {0, 0, 0, 0};  // columns per block chosen by ddp_autotune, per storage format
     int use_conditional = 1;    // device-driven while loop in a CUDA graph
     int host_chunk = 16;        // iterations per host check without conditional nodes
+    // preferred shared-memory carveout of the inner-loop stencils, percent (-1: the driver's
+    // choice): 28 rounds up to the smallest carveout that holds three 19.6 KB blocks and
+    // leaves the rest of the unified memory (about 192 KB) as L1 for the neighbour gathers
+    int carveout = 28;
     int proj_tc = 1;            // projector-cut Gram blocks and colourless sums on the tensor cores (0: FP64 kernels)
 };
 

@@ -29,6 +29,22 @@ inline void launch_hop(ddp_ctx *ctx, int nblocks, int threads, const HopArgs &a)
     k_hop<Q, EPI, DOT, CL><<<nblocks, threads, 0, ctx->stream>>>(a);
 }
 
+// Preferred shared-memory carveout of the inner-loop stencils (percent of the unified
+// L1/shared memory; the rest is L1 for the neighbour gathers), set outside graph capture.
+template <class Q, bool CL>
+inline cudaError_t set_hop_carveout(int percent) {
+    if (percent < 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_hop<Q, EPI_PLAIN, DOT_NONE, CL>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, percent);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_hop<Q, EPI_MHAT, DOT_RHAT, CL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 percent);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_hop<Q, EPI_MHAT, DOT_TS, CL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 percent);
+    return e;
+}
+
 template <class P>
 struct Engine {
     ddp_ctx *ctx;
@@ -163,6 +179,8 @@ struct Engine {
 
     int build_loop_graph() {
         cudaStream_t st = ctx->stream;
+        DDP_CUDA(ctx, (set_hop_carveout<P, false>(ctx->prm.carveout)));
+        DDP_CUDA(ctx, (set_hop_carveout<P, true>(ctx->prm.carveout)));
         if (ctx->prm.use_conditional) {
             DDP_CUDA(ctx, cudaGraphCreate(&loop_graph, 0));
             cudaGraphConditionalHandle h;
@@ -626,6 +644,7 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int kernel, int iters,
     h.v2 = none;
     h.rh = (kernel == DDP_HOP_SCHUR_RHAT) ? rhv : none;
     h.part = A;
+    DDP_CUDA(ctx, (set_hop_carveout<P, false>(ctx->prm.carveout)));
     auto launch = [&]() {
         if (kernel == DDP_HOP_PLAIN)
             launch_hop<P, EPI_PLAIN, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);
