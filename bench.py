@@ -511,16 +511,31 @@ def run_other(args):
     import paper_1601_04587_gb300 as ddp
     from paper_1601_04587_gb300 import workloads
 
-    torch.cuda.set_device(0)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        # the uneven batch shards its domains across the ranks; the other workloads
+        # are single-GPU measurements that rank 0 makes alone
+        if args.workload != "batch":
+            if rank != 0:
+                return
+            world = 1
+        else:
+            import torch.distributed as dist
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            dist.init_process_group("nccl")
+    if dist is None:
+        torch.cuda.set_device(0)
     prec = ddp.PRECISIONS[args.precision]
-    ctx = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    ctx = ddp.ddp_create(torch.cuda.current_device(), torch.cuda.current_stream().cuda_stream)
     for kv in args.param:
         k, v = kv.split("=")
         ddp.ddp_set_param(ctx, k, float(v))
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     if args.workload == "batch":
-        res = workloads.batch_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
+        res = workloads.batch_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup, dist=dist)
     elif args.workload == "multilevel":
         res = workloads.multilevel_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
     elif args.workload == "next":
@@ -533,7 +548,11 @@ def run_other(args):
     res["precision"] = args.precision
     res["gpu_launches"] = ddp.ddp_kernel_launches(ctx)
     ddp.ddp_destroy(ctx)
-    print(json.dumps(res))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res))
 
 
 # ---------------------------------------------------------- reference arm

@@ -31,17 +31,27 @@ def partition(costs, world: int):
     return [sorted(a) for a in assign]
 
 
-def run_sharded(units, costs, compute, dist=None):
-    """Compute `compute(unit)` for this rank's share and return the results of
-    all units in unit order (gathered from every rank)."""
+def run_sharded_batch(units, costs, compute_batch, dist=None):
+    """`compute_batch(list_of_units)` -> their results (same order), called once on this
+    rank's share (one batched solve per rank); returns the results of all units in
+    unit order, gathered from every rank."""
     if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
-        return [compute(u) for u in units]
+        return list(compute_batch(list(units)))
     world, rank = dist.get_world_size(), dist.get_rank()
     mine = partition(costs, world)[rank]
-    local = {i: compute(units[i]) for i in mine}
+    res = list(compute_batch([units[i] for i in mine])) if mine else []
+    if len(res) != len(mine):
+        raise ValueError("compute_batch returned a result count different from its units")
+    local = dict(zip(mine, res))
     gathered = [None] * world
     dist.all_gather_object(gathered, local)
     merged = {}
     for part in gathered:
         merged.update(part)
     return [merged[i] for i in range(len(units))]
+
+
+def run_sharded(units, costs, compute, dist=None):
+    """Compute `compute(unit)` for this rank's share and return the results of
+    all units in unit order (gathered from every rank)."""
+    return run_sharded_batch(units, costs, lambda us: [compute(u) for u in us], dist)

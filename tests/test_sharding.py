@@ -78,3 +78,44 @@ def test_two_gloo_ranks_match_unsharded(tmp_path):
     np.testing.assert_allclose(np.load(tmp_path / "pion.npy"), np.array([r["pion"] for r in ref]), rtol=1e-10)
     np.testing.assert_allclose(np.load(tmp_path / "trace.npy"), np.array([r["trace"] for r in ref]), rtol=1e-10,
                                atol=1e-14)
+
+
+def _batch_worker(rank, world, port, outdir):
+    torch.set_num_threads(max(1, (os.cpu_count() or 2) // world))
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    units, _ = _units()
+    costs = [shard.solve_cost(int(np.prod(e))) for _, e, _ in units]
+    calls = []
+
+    def batch(us):  # one batched call per rank, like one ddp_solve_batch of its share
+        calls.append(len(us))
+        return [_compute(u) for u in us]
+
+    res = shard.run_sharded_batch(units, costs, batch, dist)
+    np.save(os.path.join(outdir, f"calls{rank}.npy"), np.array(calls))
+    if rank == 0:
+        np.save(os.path.join(outdir, "bpion.npy"), np.array([r["pion"] for r in res]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_batched_shards(tmp_path):
+    """run_sharded_batch: each rank makes exactly one batched call on its cost partition,
+    and the merged results (unit order) equal the unsharded run."""
+    port = _free_port()
+    mp.start_processes(_batch_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    units, _ = _units()
+    costs = [shard.solve_cost(int(np.prod(e))) for _, e, _ in units]
+    parts = shard.partition(costs, 2)
+    for r in range(2):
+        assert list(np.load(tmp_path / f"calls{r}.npy")) == [len(parts[r])]
+    ref = [_compute(u) for u in units]
+    np.testing.assert_allclose(np.load(tmp_path / "bpion.npy"), np.array([r["pion"] for r in ref]), rtol=1e-10)
+
+
+def test_batched_shards_single_process_is_one_call():
+    calls = []
+    out = shard.run_sharded_batch([3, 1, 2], [1, 1, 1], lambda us: calls.append(list(us)) or [u * 2 for u in us])
+    assert out == [6, 2, 4] and calls == [[3, 1, 2]]
