@@ -72,6 +72,18 @@ struct HopArgs {
 // Tiles are exactly HOP_TS = 32 sites (one warp per column of a tile); a
 // block holds at most HOP_MAX_CG = 12 columns.  The kernels use the tile size
 // as a compile-time constant.
+// Storage of the BiCGStab shadow residual rh: any fixed vector serves as rh, so with
+// FP32 storage it is kept as a BF16 copy of r_0 (same exponent range, half the bytes
+// of the two reads per iteration); the other formats keep their own.
+template <class P>
+struct ShadowOf {
+    using type = P;
+};
+template <>
+struct ShadowOf<PF32> {
+    using type = PBF16;
+};
+
 constexpr int HOP_TS = 32;
 constexpr int HOP_MAX_CG = 12;
 
@@ -216,7 +228,7 @@ __device__ __forceinline__ void hop_store_epilogue(const HopArgs &a, const Item 
     store_spinor<P>(a.out, i, o);
     if (DOT == DOT_RHAT) {
         R r[24];
-        load_spinor<P>(a.rh, i, r);
+        load_spinor<typename ShadowOf<P>::type>(a.rh, i, r);
 #pragma unroll
         for (int j = 0; j < 12; j++) {
             cre += r[2 * j] * o[2 * j] + r[2 * j + 1] * o[2 * j + 1];
@@ -387,6 +399,24 @@ __device__ __forceinline__ uint4 reals_to_chunk<PF16>(const float *) {
     return make_uint4(0, 0, 0, 0);
 }
 
+// The reals of storage chunk j (of format P) of site-column i of the shadow residual,
+// stored in ShadowOf<P>.
+template <class P>
+__device__ __forceinline__ void shadow_reals(const FieldView &f, int j, int64_t i, typename P::real *v) {
+    chunk_to_reals<P>(__ldg(reinterpret_cast<const typename P::chunk *>(f.p) + j * f.stride + i), v);
+}
+template <>
+__device__ __forceinline__ void shadow_reals<PF32>(const FieldView &f, int j, int64_t i, float *v) {
+    // FP32 chunk j (reals 4j .. 4j+3) is half j % 2 of BF16 chunk j / 2
+    const uint2 c = __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const uint4 *>(f.p) +
+                                                          (int64_t)(j >> 1) * f.stride + i) + (j & 1));
+    const float2 a0 = b2f(c.x), a1 = b2f(c.y);
+    v[0] = a0.x;
+    v[1] = a0.y;
+    v[2] = a1.x;
+    v[3] = a1.y;
+}
+
 enum BlasOp { OP_P_UPDATE = 0, OP_S_UPDATE = 1, OP_XR_UPDATE = 2, OP_INIT = 3, OP_NORM = 4 };
 
 struct BlasArgs {
@@ -442,7 +472,7 @@ __global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
             const C *__restrict__ cp_ = reinterpret_cast<const C *>(a.p.p);
             const C *__restrict__ cs_ = reinterpret_cast<const C *>(a.s.p);
             const C *__restrict__ ct_ = reinterpret_cast<const C *>(a.t.p);
-            const C *__restrict__ crh = reinterpret_cast<const C *>(a.rh.p);
+
             C *__restrict__ ox = reinterpret_cast<C *>(a.x.p);
             C *__restrict__ orr = reinterpret_cast<C *>(a.r.p);
             const R ar = (R)S.alpha.x, ai = (R)S.alpha.y, wr = (R)S.omega.x, wi = (R)S.omega.y;
@@ -455,7 +485,7 @@ __global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
                 chunk_to_reals<P>(__ldg(cp_ + o), p);
                 chunk_to_reals<P>(__ldg(cs_ + o), s);
                 chunk_to_reals<P>(__ldg(ct_ + o), t);
-                chunk_to_reals<P>(__ldg(crh + o), rh);
+                shadow_reals<P>(a.rh, j, i, rh);
 #pragma unroll
                 for (int k = 0; k < NR / 2; k++) {
                     x[2 * k] += (ar * p[2 * k] - ai * p[2 * k + 1]) + (wr * s[2 * k] - wi * s[2 * k + 1]);
@@ -490,7 +520,7 @@ __global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
             store_spinor<P>(a.x, i, x);
             store_spinor<P>(a.r, i, s);
             R rh[24];
-            load_spinor<P>(a.rh, i, rh);
+            load_spinor<typename ShadowOf<P>::type>(a.rh, i, rh);
             R n2 = 0;
 #pragma unroll
             for (int j = 0; j < 12; j++) {
@@ -502,7 +532,7 @@ __global__ void __launch_bounds__(512) k_blas(BlasArgs a) {
         } else if (OP == OP_INIT) {  // rh = r ; p = r ; x = 0
             R r[24], z[24];
             load_spinor<P>(a.r, i, r);
-            store_spinor<P>(a.rh, i, r);
+            store_spinor<typename ShadowOf<P>::type>(a.rh, i, r);
             store_spinor<P>(a.p, i, r);
 #pragma unroll
             for (int j = 0; j < 24; j++) z[j] = R(0);

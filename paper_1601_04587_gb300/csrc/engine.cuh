@@ -51,7 +51,7 @@ struct Engine {
     int prec;
     Plan plan;
     FieldView be, bo, xe, xo, re64, ro64;      // FP64
-    FieldView r, rh, p, v, s, t, xi, tmp, ro;  // storage format P
+    FieldView r, rh, p, v, s, t, xi, tmp, ro;  // storage format P (rh: ShadowOf<P>)
     Partials A, B;
     Item *d_items = nullptr;
     SolveState *d_st = nullptr;
@@ -258,7 +258,7 @@ struct Engine {
         re64 = carve_field<PF64>(a, cap);
         ro64 = carve_field<PF64>(a, cap);
         r = carve_field<P>(a, cap);
-        rh = carve_field<P>(a, cap);
+        rh = carve_field<typename ShadowOf<P>::type>(a, cap);
         p = carve_field<P>(a, cap);
         v = carve_field<P>(a, cap);
         s = carve_field<P>(a, cap);
