@@ -305,7 +305,9 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * inner loop is a device-driven CUDA-graph WHILE node; 0: host-polled graph
  * chunks), "stencil_carveout" (preferred shared-memory share of the unified L1 /
  * shared memory for the inner-loop stencils, percent; default 28, -1 = the driver's
- * choice), "projector_tensor_cores" (1, the default: the Gram blocks and colourless
+ * choice), "contraction_double_fp32" (1, the default: the nucleon contraction of
+ * ddp_contract in double-FP32 arithmetic, relative error about 1e-13; 0: FP64),
+ * "projector_tensor_cores" (1, the default: the Gram blocks and colourless
  * spinor sums of the projector cut, m <= 32, run as an emulated-FP64 product on the
  * tensor cores; 0: direct FP64 kernels).  DDP_ERR_INVALID_ARG for unknown names or
  * values. */

@@ -1159,7 +1159,7 @@ int ddp_boundary_source(ddp_ctx *ctx, int domain_from, const double *psi, int do
 }
 
 // Tuning knobs of the solver (names: max_outer, max_inner, delta_fp32,
-// delta_fp16, delta_bf16, delta_fp64, tile_sites, tile_cols, conditional, stencil_carveout, projector_tensor_cores).
+// delta_fp16, delta_bf16, delta_fp64, tile_sites, tile_cols, conditional, stencil_carveout, projector_tensor_cores, contraction_double_fp32).
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
     if (!ctx || !name) return DDP_ERR_INVALID_ARG;
     EngineParams &p = ctx->prm;
@@ -1177,6 +1177,7 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
         p.CG = (int)value;
     } else if (n == "conditional") p.use_conditional = value != 0;
     else if (n == "projector_tensor_cores") p.proj_tc = value != 0;
+    else if (n == "contraction_double_fp32") p.contract_dd = value != 0;
     else if (n == "stencil_carveout") {
         if (value < -1 || value > 100) return DDP_ERR_INVALID_ARG;
         p.carveout = (int)value;

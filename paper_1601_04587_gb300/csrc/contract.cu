@@ -1,4 +1,5 @@
-// Wick contractions of domain propagators (FP64):
+// Wick contractions of domain propagators (FP64; the nucleon, the one ALU-heavy
+// contraction, in double-FP32 arithmetic unless "contraction_double_fp32" is 0):
 //   - local disconnected trace tr{g5 S(x,x)} (Sec. 3, Eq. W0),
 //   - stochastic time-slice trace sum_{x vec} sum_c eta_c^+ g5 psi_c (Sec. 5),
 //   - pion sum_{y vec} tr{S S^+} (Sec. 4, Eq. W0pc with the exact S),
@@ -7,6 +8,7 @@
 // shuffles, fixed order), a second kernel adds a slice's partials in order.
 #include <cstring>
 
+#include "ddfloat.cuh"
 #include "ddp_host.h"
 
 namespace ddp {
@@ -52,9 +54,28 @@ __constant__ double kSign[6] = {1, 1, 1, -1, -1, -1};
 // so that with t_rho the row-rho parts of the traces,
 //   W_N1 = sum eps eps [sum_rho sum_sigma S^{ag}_{rho sigma} (-1)^(rho+sigma) S^{bf}_{rho^1 sigma^1}] tr[S^{ce} P-],
 //   W_N2 = sum eps eps  sum_rho sum_sigma S^{ag}_{rho sigma} (-1)^(rho+sigma) (E F)_{rho^1 sigma^1}.
-__device__ __forceinline__ Cplx sel(const Cplx *site, int rho, int a, int sigma, int b) {
+template <class C>
+__device__ __forceinline__ C sel(const C *site, int rho, int a, int sigma, int b) {
     return site[(3 * sigma + b) * 12 + 3 * rho + a];  // S(y,x)_{rho a, sigma b}
 }
+
+// The nucleon is computed in FP64 (Cplx) or in double-FP32 (Cdd, the default: GB300's
+// FP64 rate is about 1/64 of its FP32 rate); the conversions of the loaded entries and of
+// the per-lane sums are the only FP64 arithmetic of the double-FP32 form.
+template <class C>
+__device__ __forceinline__ C czero();
+template <>
+__device__ __forceinline__ Cplx czero<Cplx>() { return {0, 0}; }
+template <>
+__device__ __forceinline__ Cdd czero<Cdd>() { return {dd(0.f, 0.f), dd(0.f, 0.f)}; }
+template <class C>
+__device__ __forceinline__ C cfrom(Cplx v);
+template <>
+__device__ __forceinline__ Cplx cfrom<Cplx>(Cplx v) { return v; }
+template <>
+__device__ __forceinline__ Cdd cfrom<Cdd>(Cplx v) { return {dd_of(v.re), dd_of(v.im)}; }
+__device__ __forceinline__ Cplx cto(Cplx v) { return v; }
+__device__ __forceinline__ Cplx cto(Cdd v) { return {dd_to_double(v.re), dd_to_double(v.im)}; }
 
 // grid (nchunk, e0), 128 threads: 4 warps x 8 sites = 32 sites of a time slice per block.
 // A warp takes its sites two at a time.  The factors that do not depend on the
@@ -66,39 +87,42 @@ __device__ __forceinline__ Cplx sel(const Cplx *site, int rho, int a, int sigma,
 //   unit = sign (t1 t2[c][e] - E[rho^1][b][e][0] X_0 - E[rho^1][b][e][1] X_1).
 constexpr int NUC_WARPS = 4, NUC_SITES_PER_WARP = 8;
 
+template <class C>
 struct NucSite {
-    Cplx S[144];
-    Cplx t2[9];   // [c][e]
-    Cplx E[72];   // [rho][b][e][lambda]
-    Cplx F[72];   // [c][sigma][f][lambda]
+    C S[144];
+    C t2[9];   // [c][e]
+    C E[72];   // [rho][b][e][lambda]
+    C F[72];   // [c][sigma][f][lambda]
 };
 
-__device__ __forceinline__ Cplx nucleon_unit(const NucSite &q, int unit) {
+template <class C>
+__device__ __forceinline__ C nucleon_unit(const NucSite<C> &q, int unit) {
     const int pr = unit >> 2, rho = unit & 3;
     const int p1 = pr / 6, p2 = pr - 6 * (pr / 6);
     const int a = kPerm[p1][0], b = kPerm[p1][1], c = kPerm[p1][2];
     const int f = kPerm[p2][0], e = kPerm[p2][1], g = kPerm[p2][2];
     const double sg = kSign[p1] * kSign[p2];
     const int r1 = rho ^ 1;
-    Cplx t1 = {0, 0}, x0 = {0, 0}, x1 = {0, 0};
+    C t1 = czero<C>(), x0 = czero<C>(), x1 = czero<C>();
 #pragma unroll
     for (int sigma = 0; sigma < 4; sigma++) {
         const int s1 = sigma ^ 1;
         const double ph = ((rho + sigma) & 1) ? -1.0 : 1.0;
-        const Cplx sag = cscale(ph, sel(q.S, rho, a, sigma, g));
+        const C sag = cscale(ph, sel(q.S, rho, a, sigma, g));
         t1 = cadd(t1, cmulc(sag, sel(q.S, r1, b, s1, f)));
         x0 = cadd(x0, cmulc(sag, q.F[((c * 4 + s1) * 3 + f) * 2 + 0]));
         x1 = cadd(x1, cmulc(sag, q.F[((c * 4 + s1) * 3 + f) * 2 + 1]));
     }
-    const Cplx t3 = cadd(cmulc(q.E[((r1 * 3 + b) * 3 + e) * 2 + 0], x0), cmulc(q.E[((r1 * 3 + b) * 3 + e) * 2 + 1], x1));
+    const C t3 = cadd(cmulc(q.E[((r1 * 3 + b) * 3 + e) * 2 + 0], x0), cmulc(q.E[((r1 * 3 + b) * 3 + e) * 2 + 1], x1));
     return cscale(sg, csub(cmulc(t1, q.t2[c * 3 + e]), t3));
 }
 
 // t2, E and F of a site from its 144 entries (item k of the 153 per site).
-__device__ __forceinline__ void nucleon_factor(NucSite &q, int k) {
+template <class C>
+__device__ __forceinline__ void nucleon_factor(NucSite<C> &q, int k) {
     if (k < 9) {
         const int c = k / 3, e = k - 3 * (k / 3);
-        Cplx t = {0, 0};
+        C t = czero<C>();
 #pragma unroll
         for (int r = 0; r < 4; r++) t = cadd(t, csub(sel(q.S, r, c, r, e), sel(q.S, r, c, r ^ 2, e)));
         q.t2[k] = cscale(0.5, t);
@@ -111,8 +135,9 @@ __device__ __forceinline__ void nucleon_factor(NucSite &q, int k) {
     }
 }
 
+template <class C>
 __global__ void __launch_bounds__(128) k_contract_nucleon(ContractArgs a) {
-    __shared__ NucSite s_q[NUC_WARPS][2];
+    __shared__ NucSite<C> s_q[NUC_WARPS][2];
     __shared__ double s_re[NUC_WARPS], s_im[NUC_WARPS];
     const Item &it = a.it;
     const int slice_n = it.e[1] * it.e[2] * it.e[3];
@@ -120,24 +145,25 @@ __global__ void __launch_bounds__(128) k_contract_nucleon(ContractArgs a) {
     const int t = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = blockIdx.x * (NUC_WARPS * NUC_SITES_PER_WARP) + warp * NUC_SITES_PER_WARP;
-    Cplx acc = {0, 0};
+    C acc = czero<C>();
     for (int j = 0; j < NUC_SITES_PER_WARP; j += 2) {
         const int nsite = min(2, slice_n - (r0 + j));
         if (nsite <= 0) break;
         for (int q = lane; q < 144 * nsite; q += 32) {
             const int s = q / 144, m = q - 144 * s;
             const int col = m / 12, k = m - 12 * (m / 12);
-            s_q[warp][s].S[m] = ld(a.S + ((int64_t)col * n + t * slice_n + r0 + j + s) * 12 + k);
+            s_q[warp][s].S[m] = cfrom<C>(ld(a.S + ((int64_t)col * n + t * slice_n + r0 + j + s) * 12 + k));
         }
         __syncwarp();
         for (int k = lane; k < 153 * nsite; k += 32) nucleon_factor(s_q[warp][k / 153], k % 153);
         __syncwarp();
-        Cplx v = {0, 0};
+        C v = czero<C>();
         for (int u = lane; u < 144 * nsite; u += 32) v = cadd(v, nucleon_unit(s_q[warp][u / 144], u % 144));
         acc = cadd(acc, v);
         __syncwarp();
     }
-    double re = warp_sum(acc.re), im = warp_sum(acc.im);
+    const Cplx acc64 = cto(acc);
+    double re = warp_sum(acc64.re), im = warp_sum(acc64.im);
     if (lane == 0) {
         s_re[warp] = re;
         s_im[warp] = im;
@@ -367,8 +393,12 @@ extern "C" int ddp_contract(ddp_ctx *ctx, int kind, int domain_id, const double 
             a.nchunk = nchunk;
             a.part = (double2 *)dPart;
             dim3 grid(nchunk, d.e[0]);
-            if (kind == DDP_CONTRACT_NUCLEON)
-                k_contract_nucleon<<<grid, NUC_WARPS * 32, 0, st>>>(a);
+            if (kind == DDP_CONTRACT_NUCLEON) {
+                if (ctx->prm.contract_dd)
+                    k_contract_nucleon<Cdd><<<grid, NUC_WARPS * 32, 0, st>>>(a);
+                else
+                    k_contract_nucleon<Cplx><<<grid, NUC_WARPS * 32, 0, st>>>(a);
+            }
             else
                 k_contract_slice<<<grid, threads, 0, st>>>(a);
             k_contract_final<<<g.L[0], 256, 0, st>>>(it, (const double2 *)dPart, nchunk, (double2 *)dOut);
@@ -505,7 +535,7 @@ extern "C" int ddp_contract_static(int kind, const int L[4], const int origin[4]
     a.part = scratch;
     dim3 grid(nchunk, extent[0]);
     if (kind == DDP_CONTRACT_NUCLEON)
-        k_contract_nucleon<<<grid, NUC_WARPS * 32, 0, st>>>(a);
+        k_contract_nucleon<Cdd><<<grid, NUC_WARPS * 32, 0, st>>>(a);  // the default form of ddp_contract
     else
         k_contract_slice<<<grid, threads, 0, st>>>(a);
     if (cudaPeekAtLastError() != cudaSuccess) return DDP_ERR_CUDA;

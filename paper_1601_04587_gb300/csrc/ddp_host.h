@@ -84,6 +84,7 @@ struct EngineParams {
     // choice): 28 rounds up to the smallest carveout that holds three 19.6 KB blocks and
     // leaves the rest of the unified memory (about 192 KB) as L1 for the neighbour gathers
     int carveout = 28;
+    int contract_dd = 1;        // nucleon contraction in double-FP32 arithmetic (0: FP64)
     int proj_tc = 1;            // projector-cut Gram blocks and colourless sums on the tensor cores (0: FP64 kernels)
 };
 
