@@ -309,7 +309,8 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * ddp_contract in double-FP32 arithmetic, relative error about 1e-13; 0: FP64),
  * "projector_tensor_cores" (1, the default: the Gram blocks and colourless
  * spinor sums of the projector cut, m <= 32, run as an emulated-FP64 product on the
- * tensor cores; 0: direct FP64 kernels).  DDP_ERR_INVALID_ARG for unknown names or
+ * tensor cores and the Cholesky-QR update A <- A R^-1 in double-FP32; 0: direct FP64
+ * kernels).  DDP_ERR_INVALID_ARG for unknown names or
  * values. */
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value);
 

@@ -45,6 +45,28 @@ __device__ __forceinline__ dd dd_of(double v) {
 }
 __device__ __forceinline__ double dd_to_double(dd a) { return (double)a.hi + (double)a.lo; }
 
+// The same split from the bit pattern of v with integer and FP32 operations only (for
+// loads of FP64 fields, where FP64-pipe conversions would cost as much as the FP64
+// arithmetic they replace): hi = the significand rounded to 24 bits, lo = the remainder.
+// |v| < 2^-100 (zero included) gives 0, an absolute error far below the 2^-46 relative
+// accuracy for values of order 1; |v| >= 2^127 gives float(v).
+__device__ __forceinline__ dd dd_of_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ev = (int)((b >> 52) & 0x7FF);
+    if (ev < 1023 - 100) return dd(0.f, 0.f);
+    if (ev > 1023 + 126) return dd(__double2float_rn(v), 0.f);
+    const unsigned long long r = (b + 0x10000000ull) & ~0x1FFFFFFFull;  // may carry into the exponent
+    const int er = (int)((r >> 52) & 0x7FF);
+    const float hi = __uint_as_float((unsigned)((b >> 32) & 0x80000000u) | ((unsigned)(er - 896) << 23) |
+                                     (unsigned)((r >> 29) & 0x7FFFFFu));
+    // remainder in units of 2^(ev - 1075): the low 29 significand bits, less 2^29 if rounded up
+    const int rem = (int)(unsigned)(b & 0x1FFFFFFFull) - (int)(unsigned)((b & 0x10000000ull) << 1);
+    const int pe = ev - 1046;  // rem 2^(ev - 1075) = (rem 2^-29) 2^pe, pe >= -123
+    float lo = __int_as_float((127 + pe) << 23) * (__int2float_rn(rem) * 1.862645149230957e-9f);
+    if (b >> 63) lo = -lo;
+    return dd(hi, lo);
+}
+
 // complex double-FP32
 struct Cdd {
     dd re, im;

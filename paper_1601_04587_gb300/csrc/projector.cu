@@ -10,6 +10,7 @@
 #include <cstring>
 #include <vector>
 
+#include "ddfloat.cuh"
 #include "ddp_host.h"
 
 using namespace ddp;
@@ -156,6 +157,40 @@ __global__ void k_apply_rinv(double2 *A, int64_t cs, int m, const double2 *Rinv)
     }
 }
 
+// The same update in double-FP32 arithmetic (the A entries split from their bits,
+// R^-1 staged in shared memory): GB300's FP64 rate is about 1/64 of its FP32 rate.
+constexpr int RINV_MMAX = 32;
+__global__ void __launch_bounds__(128) k_apply_rinv_dd(double2 *A, int64_t cs, int m, const double2 *Rinv) {
+    __shared__ Cdd sR[RINV_MMAX * RINV_MMAX];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const double2 c = Rinv[e];
+        sR[e] = {dd_of(c.x), dd_of(c.y)};
+    }
+    __syncthreads();
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= cs) return;
+    constexpr int TJ = 8;
+    for (int j0 = ((m - 1) / TJ) * TJ; j0 >= 0; j0 -= TJ) {
+        Cdd acc[TJ];
+#pragma unroll
+        for (int t = 0; t < TJ; t++) acc[t] = {dd(0.f, 0.f), dd(0.f, 0.f)};
+        const int jmax = min(m, j0 + TJ);
+        for (int i = 0; i < jmax; i++) {
+            const double2 a = A[(int64_t)i * cs + r];
+            const Cdd v = {dd_of_bits(a.x), dd_of_bits(a.y)};
+#pragma unroll
+            for (int t = 0; t < TJ; t++) {
+                const int j = j0 + t;
+                if (j >= m || i > j) continue;
+                acc[t] = cadd(acc[t], cmulc(v, sR[i * m + j]));
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TJ; t++)
+            if (j0 + t < m) A[(int64_t)(j0 + t) * cs + r] = make_double2(dd_to_double(acc[t].re), dd_to_double(acc[t].im));
+    }
+}
+
 // Upper-triangular R with G = R^+ R and its inverse (host, m x m complex).
 bool cholesky_upper_inverse(const std::vector<double2> &G, int m, std::vector<double2> &Rinv) {
     std::vector<double> Rr((size_t)m * m, 0.0), Ri((size_t)m * m, 0.0);
@@ -218,7 +253,10 @@ int orthonormalize(ddp_ctx *ctx, double2 *A, int64_t cs, int m, Arena &ar) {
         double2 *dR = dG + (size_t)m * m;
         DDP_CUDA(ctx, cudaMemcpyAsync(dR, Rinv.data(), (size_t)m * m * sizeof(double2), cudaMemcpyHostToDevice,
                                       ctx->stream));
-        k_apply_rinv<<<(unsigned)((cs + 127) / 128), 128, 0, ctx->stream>>>(A, cs, m, dR);
+        if (ctx->prm.proj_tc && m <= RINV_MMAX)
+            k_apply_rinv_dd<<<(unsigned)((cs + 127) / 128), 128, 0, ctx->stream>>>(A, cs, m, dR);
+        else
+            k_apply_rinv<<<(unsigned)((cs + 127) / 128), 128, 0, ctx->stream>>>(A, cs, m, dR);
         ctx->launches++;
         DDP_CUDA(ctx, cudaGetLastError());
         DDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
