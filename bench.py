@@ -114,7 +114,7 @@ def write_hop_traffic(csv_path):
             b = d["dram__bytes_read.sum"] + d["dram__bytes_write.sum"]
             captured[key] = min(captured.get(key, b), b)  # launches after the first: warm L2
     sites = HOP_TRAFFIC_LATTICE[0] * HOP_TRAFFIC_LATTICE[1] * HOP_TRAFFIC_LATTICE[2] * HOP_TRAFFIC_LATTICE[3] // 2
-    per_site_col = {"fp32/plain": 224, "fp32/schur_rhat": 416, "fp32/schur_ts": 320}
+    per_site_col = {"fp32/plain": 224, "fp32/schur_rhat": 368, "fp32/schur_ts": 320}
     scale = 48 / HOP_TRAFFIC_LATTICE[0]
     rec = {"what": "ncu DRAM bytes (read + write) per launch of the three inner-loop stencils, FP32 storage, 12 columns",
            "captured_lattice": list(HOP_TRAFFIC_LATTICE), "ncol": 12,
@@ -541,7 +541,8 @@ def run_other(args):
     elif args.workload == "next":
         res = workloads.next_rows_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
     elif args.workload == "projector":
-        res = workloads.projector_workload(ddp, torch, ctx, synth, prec, steps=args.steps, warmup=args.warmup)
+        res = workloads.projector_workload(ddp, torch, ctx, synth, prec, nm=args.modes, steps=args.steps,
+                                           warmup=args.warmup)
     else:
         res = workloads.serve_workload(ddp, torch, ctx, synth, prec)
     res["clocks"] = clocks.stop()
@@ -636,6 +637,8 @@ def main():
     ap.add_argument("--iters", type=int, default=20, help="--workload hop: timed launches per kernel")
     ap.add_argument("--param", action="append", default=[],
                     help="solver parameter name=value passed to ddp_set_param (repeatable)")
+    ap.add_argument("--modes", type=int, default=120,
+                    help="--workload projector: number of modes N_m (default 120, the paper's)")
     ap.add_argument("--kappa", type=float, default=None, help="slabs: kappa (default 0.14)")
     ap.add_argument("--csw", type=float, default=0.0, help="slabs: clover coefficient c_sw (default 0)")
     ap.add_argument("--no-conditional", action="store_true",

@@ -327,8 +327,9 @@ typedef enum {
  * events over `iters` launches on the context's stream after 3 warm-up
  * launches; bytes_per_launch receives the variant's algorithmic HBM bytes:
  * the spinors it reads or writes once per output site-column (2 for PLAIN,
- * 4 for SCHUR_RHAT, 3 for SCHUR_TS) plus the 8 links touching every output
- * site once for all columns. */
+ * 4 for SCHUR_RHAT, of which the shadow residual rh is counted in its own
+ * storage: BF16 for FP32 storage, 3 for SCHUR_TS) plus the 8 links touching
+ * every output site once for all columns. */
 int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int kernel, int iters,
                  float *ms_per_launch, double *bytes_per_launch);
 
@@ -361,11 +362,13 @@ int ddp_serve_reset(ddp_ctx *ctx);
  *            form 2), ddp_projected_nucleon(X, Y)              (Eq. W0tbary).
  * Fields: [m][n_sites][4][3] complex in domain-local order, host or device memory
  * (detected per pointer); every call returns when its output is complete.
- * Gram blocks and colourless sums (m <= 32) run on the tensor cores: every operand is
+ * Gram blocks and colourless sums (m <= 128: the paper's N_m = 120 modes fit) run on the
+ * tensor cores: every operand is
  * split into seven 7-bit integer slices under a power-of-two exponent per row or
  * column, the slice products are summed exactly, and each term of a sum is exact to
  * about 2^-47 of its row maximum times its column maximum (FP64-level; the parameter
- * "projector_tensor_cores" = 0 selects direct FP64 kernels).  A NaN or infinity in an
+ * "projector_tensor_cores" = 0 selects direct FP64 kernels, the colourless sums for
+ * m <= 32 only).  A NaN or infinity in an
  * input makes exactly the outputs of its time slice that depend on it NaN. */
 
 /* V <- the orthonormal basis of span(V) that Gram-Schmidt in column order gives
@@ -395,7 +398,8 @@ int ddp_gram_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, double 
  * colourless spinors B[s_i, s_j, s_k; x]_alpha = eps^{abc} (s_i^a)^T C g5 s_j^b (s_k^c)_alpha
  * of Eq. W0tbary (C = i g0 g2) with s_i = A_i (form 0), g5 conj(A_i) (form 1: the
  * spinor of the row phi_i^+ D^-1 when A_i = D^-1 g5 phi_i) or -A_i (form 2).
- * X_out: L0 x m^3 x 4 complex.  m <= 32 (else DDP_ERR_UNSUPPORTED). */
+ * X_out: L0 x m^3 x 4 complex.  m <= 128 on the tensor cores, m <= 32 with the direct
+ * FP64 kernel (else DDP_ERR_UNSUPPORTED). */
 int ddp_colourless_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, int form, double *X_out);
 
 /* C[y0][x0] = (1/L^3) sum_ij Mt[y0][i][j] M[x0][j][i] = (1/L^3) sum_{x vec, y vec} W~(y, x)
@@ -407,7 +411,9 @@ int ddp_projected_pion(ddp_ctx *ctx, int L0, int m, const double *Mt, const doub
  * P- Y_ijk(y0), P- = (1 - g0)/2: the nucleon contractions of Sec. 4 with S~
  * substituted (Eq. W0tbary; the paper prints -g5 P- between the spinors, which
  * corresponds to an x-side spinor with an extra -g5).  X, Y: L0 x m^3 x 4 complex
- * from ddp_colourless_slices; C_out: L0 x L0 complex. */
+ * from ddp_colourless_slices; C_out: L0 x L0 complex.  Computed as the FP64 product
+ * C = P D^T over the 4 m^3 (i, j, k, alpha) terms, split into chunks summed in a fixed
+ * order; needs L0 x 4 m^3 complex of scratch (5.3 GB at m = 120, L0 = 48). */
 int ddp_projected_nucleon(ddp_ctx *ctx, int L0, int m, const double *X, const double *Y, double *C_out);
 
 /* ---- allocation-free contraction ------------------------------------------

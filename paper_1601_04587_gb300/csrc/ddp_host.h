@@ -154,10 +154,14 @@ int set_cuda_error(ddp_ctx *ctx, cudaError_t e, const char *where);
 // (least recently used first out, CLOVER_CACHE pairs).
 constexpr int CLOVER_CACHE = 4;
 int clover_for(ddp_ctx *ctx, GaugeDev &g, double kappa, double csw, const CloverDev **out);
-// Colourless-spinor time-slice sums on the tensor cores (device fields; X zeroed by the caller).
+// Largest number of columns (modes) of the tensor-core Gram blocks and colourless sums
+// of the projector cut: one 128-row MMA tile holds the rows of a Gram block.
+constexpr int TC_MMAX = 128;
+// Colourless-spinor time-slice sums on the tensor cores (m <= TC_MMAX; device fields;
+// X zeroed by the caller).
 int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, int64_t slice_n, int nslice, int o0,
                   int L0, double2 *X);
-// Gram blocks of nseg row segments on the tensor cores (m <= 32; device buffers).
+// Gram blocks of nseg row segments on the tensor cores (m <= TC_MMAX; device buffers).
 int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int nseg, double2 *out);
 
 #define DDP_CUDA(ctx, call)                                          \

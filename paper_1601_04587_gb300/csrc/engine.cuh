@@ -598,8 +598,9 @@ int hop_power_impl(ddp_ctx *ctx, const Job &job, int p, const double *psi, doubl
 // kappa^2 H_eo tmp with the (rh, v) partials;  DDP_HOP_SCHUR_TS  t = s -
 // kappa^2 H_eo tmp with the (t, s), (t, t) partials.  Algorithmic bytes per
 // launch: the spinors the variant reads or writes once per output
-// site-column (2, 4 and 3 of them) plus the 8 links touching each output
-// site once for all columns.
+// site-column (2, 4 and 3 of them; the shadow residual of the (rh, v) variant
+// in its own storage, BF16 for FP32 storage) plus the 8 links touching each
+// output site once for all columns.
 template <class P>
 int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int kernel, int iters, float *ms, double *bytes) {
     std::vector<Job> jobs(1, job);
@@ -671,9 +672,14 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int kernel, int iters,
     const double site_cols = (double)plan.items[0].nh * job.ncol;
     const double spinor = (double)sizeof(typename P::chunk) * P::NCH + (P::SCALED ? 4.0 : 0.0);
     const double link = P::IS64 ? 144.0 : (std::is_same<P, PF32>::value ? 48.0 : 24.0);
-    const int nspinor = (kernel == DDP_HOP_PLAIN) ? 2 : (kernel == DDP_HOP_SCHUR_RHAT) ? 4 : 3;
+    using SH = typename ShadowOf<P>::type;
+    const double shadow = (double)sizeof(typename SH::chunk) * SH::NCH + (SH::SCALED ? 4.0 : 0.0);
+    // spinors of the storage format read or written once per output site-column, plus
+    // the shadow residual (in its own format) of the (rh, v) variant
+    const double per_col = (kernel == DDP_HOP_PLAIN) ? 2 * spinor
+                           : (kernel == DDP_HOP_SCHUR_RHAT) ? 3 * spinor + shadow : 3 * spinor;
     // every link touching an output site: 8 per output site (4 forward + 4 backward)
-    *bytes = site_cols * nspinor * spinor + (double)plan.items[0].nh * 8.0 * link;
+    *bytes = site_cols * per_col + (double)plan.items[0].nh * 8.0 * link;
     return DDP_OK;
 }
 

@@ -95,9 +95,9 @@ __global__ void k_gram_reduce(const double2 *part, int nks, int m, int nseg, dou
 }
 
 // Gram blocks of nseg consecutive row segments of seg rows each; out [nseg][m][m].
-// On the tensor cores (gram_tc) unless the context asks for the FP64 kernel or m > 32.
+// On the tensor cores (gram_tc) unless the context asks for the FP64 kernel or m > TC_MMAX.
 int gram(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int nseg, double2 *out, Arena &ar) {
-    if (ctx->prm.proj_tc && m <= 32) return gram_tc(ctx, A, cs, m, seg, nseg, out);
+    if (ctx->prm.proj_tc && m <= TC_MMAX) return gram_tc(ctx, A, cs, m, seg, nseg, out);
     const int ntile = (m + GT - 1) / GT;
     // enough blocks to fill the GPU: split each segment into pieces of >= 512 rows
     int64_t want = std::max<int64_t>(1, 1200 / std::max<int64_t>(1, (int64_t)ntile * ntile * nseg));
@@ -159,22 +159,41 @@ __global__ void k_apply_rinv(double2 *A, int64_t cs, int m, const double2 *Rinv)
 
 // The same update in double-FP32 arithmetic (the A entries split from their bits,
 // R^-1 staged in shared memory): GB300's FP64 rate is about 1/64 of its FP32 rate.
-constexpr int RINV_MMAX = 32;
+// Up to RINV_MMAX_ALL columns R^-1 is staged whole; beyond, the TJ columns of each
+// output tile are staged in turn (the same products in the same order).
+constexpr int RINV_MMAX_ALL = 32, RINV_MMAX = TC_MMAX, RINV_TJ = 8;
 __global__ void __launch_bounds__(128) k_apply_rinv_dd(double2 *A, int64_t cs, int m, const double2 *Rinv) {
-    __shared__ Cdd sR[RINV_MMAX * RINV_MMAX];
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const double2 c = Rinv[e];
-        sR[e] = {dd_of(c.x), dd_of(c.y)};
+    constexpr int TJ = RINV_TJ;
+    constexpr int SR = RINV_MMAX_ALL * RINV_MMAX_ALL > RINV_MMAX * TJ ? RINV_MMAX_ALL * RINV_MMAX_ALL : RINV_MMAX * TJ;
+    __shared__ Cdd sR[SR];
+    const bool whole = m <= RINV_MMAX_ALL;
+    if (whole) {
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const double2 c = Rinv[e];
+            sR[e] = {dd_of(c.x), dd_of(c.y)};
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= cs) return;
-    constexpr int TJ = 8;
+    // rows beyond the field still take part in the staging barriers of the tiles
+    const bool row = r < cs;
+    if (whole && !row) return;
     for (int j0 = ((m - 1) / TJ) * TJ; j0 >= 0; j0 -= TJ) {
+        const int jmax = min(m, j0 + TJ);
+        if (!whole) {
+            // R^-1 [i][j0 .. jmax) for i < jmax, at sR[i * TJ + (j - j0)]
+            __syncthreads();  // the previous tile's reads are done
+            for (int e = threadIdx.x; e < jmax * TJ; e += blockDim.x) {
+                const int i = e / TJ, j = j0 + e % TJ;
+                const double2 c = j < m ? Rinv[(int64_t)i * m + j] : make_double2(0.0, 0.0);
+                sR[e] = {dd_of(c.x), dd_of(c.y)};
+            }
+            __syncthreads();
+        }
+        if (!row) continue;
         Cdd acc[TJ];
 #pragma unroll
         for (int t = 0; t < TJ; t++) acc[t] = {dd(0.f, 0.f), dd(0.f, 0.f)};
-        const int jmax = min(m, j0 + TJ);
         for (int i = 0; i < jmax; i++) {
             const double2 a = A[(int64_t)i * cs + r];
             const Cdd v = {dd_of_bits(a.x), dd_of_bits(a.y)};
@@ -182,7 +201,7 @@ __global__ void __launch_bounds__(128) k_apply_rinv_dd(double2 *A, int64_t cs, i
             for (int t = 0; t < TJ; t++) {
                 const int j = j0 + t;
                 if (j >= m || i > j) continue;
-                acc[t] = cadd(acc[t], cmulc(v, sR[i * m + j]));
+                acc[t] = cadd(acc[t], cmulc(v, whole ? sR[i * m + j] : sR[i * TJ + t]));
             }
         }
 #pragma unroll
@@ -431,37 +450,74 @@ __global__ void k_proj_pion(const double2 *Mt, const double2 *M, int L0, int m, 
 }
 
 // C(y0, x0) = sum_ijk [X_{jik}(x0) - X_{kij}(x0)]^T P- Y_{ijk}(y0), P- = (1 - g0)/2,
-// i.e. (P- v)_a = (v_a - v_{a^2}) / 2 with a^2 the spin two places away.
-// One block per (y0, x0); threads stride over (i, j, k); tree sum in shared memory.
-__global__ void __launch_bounds__(256) k_proj_nucleon(const double2 *X, const double2 *Y, int L0, int m, double2 *C) {
-    __shared__ double sre[256], sim[256];
-    const int y0 = blockIdx.x / L0, x0 = blockIdx.x % L0;
-    const int64_t m3 = (int64_t)m * m * m;
+// i.e. (P- v)_a = (v_a - v_{a^2}) / 2 with a^2 the spin two places away.  Written as the
+// product C = P D^T over the index K = ((i m + j) m + k) 4 + alpha of length 4 m^3, with
+// P[y0][K] = (P- Y_{ijk}(y0))_alpha and D[x0][K] = (X_{jik}(x0) - X_{kij}(x0))_alpha.
+
+// D, formed once (K-major rows, one per time slice).
+__global__ void k_nucleon_d(const double2 *X, int L0, int m, double2 *D) {
+    const int64_t m3 = (int64_t)m * m * m, nk = 4 * m3;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)L0 * nk) return;
+    const int64_t t = g / nk, K = g % nk, e = K / 4;
+    const int al = (int)(K % 4);
+    const int i = (int)(e / ((int64_t)m * m)), j = (int)((e / m) % m), k = (int)(e % m);
+    const double2 a = X[(t * m3 + ((int64_t)j * m + i) * m + k) * 4 + al];
+    const double2 b = X[(t * m3 + ((int64_t)k * m + i) * m + j) * 4 + al];
+    D[g] = make_double2(a.x - b.x, a.y - b.y);
+}
+
+// Partial products over K chunks: block (chunk, 16 x 16 output tile) sums
+// P[y0][K] D[x0][K] over its K range in steps of NK_STEP staged in shared memory (P- of Y
+// applied while staging), one output per thread, written to part[chunk][y0][x0].
+constexpr int NK_TILE = 16, NK_STEP = 64;
+__global__ void __launch_bounds__(NK_TILE *NK_TILE) k_nucleon_gemm(const double2 *Y, const double2 *D, int L0,
+                                                                   int64_t nk, int64_t kchunk, double2 *part) {
+    // rows padded by one element: the 16 rows a quarter-warp reads fall in distinct banks
+    __shared__ double2 sP[NK_TILE][NK_STEP + 1], sD[NK_TILE][NK_STEP + 1];
+    const int ntx = (L0 + NK_TILE - 1) / NK_TILE;
+    const int ty = blockIdx.y / ntx, tx = blockIdx.y % ntx;
+    const int ly = threadIdx.x / NK_TILE, lx = threadIdx.x % NK_TILE;
+    const int y0 = ty * NK_TILE + ly, x0 = tx * NK_TILE + lx;
+    const int64_t k0 = blockIdx.x * kchunk, k1 = min(nk, k0 + kchunk);
     double re = 0, im = 0;
-    for (int64_t e = threadIdx.x; e < m3; e += blockDim.x) {
-        const int i = (int)(e / ((int64_t)m * m)), j = (int)((e / m) % m), k = (int)(e % m);
-        const double2 *y = Y + ((int64_t)y0 * m3 + e) * 4;
-        const double2 *xa = X + ((int64_t)x0 * m3 + ((int64_t)j * m + i) * m + k) * 4;
-        const double2 *xb = X + ((int64_t)x0 * m3 + ((int64_t)k * m + i) * m + j) * 4;
-        for (int al = 0; al < 4; al++) {
-            const int ap = al ^ 2;
-            const double2 py = make_double2(0.5 * (y[al].x - y[ap].x), 0.5 * (y[al].y - y[ap].y));
-            const double2 d = make_double2(xa[al].x - xb[al].x, xa[al].y - xb[al].y);
-            re += d.x * py.x - d.y * py.y;
-            im += d.x * py.y + d.y * py.x;
+    for (int64_t kb = k0; kb < k1; kb += NK_STEP) {
+        for (int e = threadIdx.x; e < NK_TILE * NK_STEP; e += blockDim.x) {
+            const int r = e / NK_STEP, c = e % NK_STEP;
+            const int64_t K = kb + c;
+            const int yr = ty * NK_TILE + r, xr = tx * NK_TILE + r;
+            double2 pv = make_double2(0.0, 0.0), dv = make_double2(0.0, 0.0);
+            if (K < k1 && yr < L0) {
+                const double2 u = Y[(int64_t)yr * nk + K], w = Y[(int64_t)yr * nk + (K ^ 2)];
+                pv = make_double2(0.5 * (u.x - w.x), 0.5 * (u.y - w.y));
+            }
+            if (K < k1 && xr < L0) dv = D[(int64_t)xr * nk + K];
+            sP[r][c] = pv;
+            sD[r][c] = dv;
         }
-    }
-    sre[threadIdx.x] = re;
-    sim[threadIdx.x] = im;
-    __syncthreads();
-    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            sre[threadIdx.x] += sre[threadIdx.x + o];
-            sim[threadIdx.x] += sim[threadIdx.x + o];
+        __syncthreads();
+#pragma unroll 8
+        for (int c = 0; c < NK_STEP; c++) {
+            const double2 p = sP[ly][c], d = sD[lx][c];
+            re = fma(p.x, d.x, fma(-p.y, d.y, re));
+            im = fma(p.x, d.y, fma(p.y, d.x, im));
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) C[blockIdx.x] = make_double2(sre[0], sim[0]);
+    if (y0 < L0 && x0 < L0) part[((int64_t)blockIdx.x * L0 + y0) * L0 + x0] = make_double2(re, im);
+}
+
+// C[y0][x0] = the chunk partials summed in chunk order.
+__global__ void k_nucleon_sum(const double2 *part, int nchunk, int L0, double2 *C) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= L0 * L0) return;
+    double re = 0, im = 0;
+    for (int c = 0; c < nchunk; c++) {
+        const double2 v = part[(int64_t)c * L0 * L0 + g];
+        re += v.x;
+        im += v.y;
+    }
+    C[g] = make_double2(re, im);
 }
 
 bool dptr(const void *p) {
@@ -666,7 +722,8 @@ int ddp_gram_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, double 
 
 int ddp_colourless_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, int form, double *X_out) {
     if (!ctx || !A || !X_out || m < 1 || form < 0 || form > 2) return DDP_ERR_INVALID_ARG;
-    if (m > CB_MMAX) return DDP_ERR_UNSUPPORTED;
+    // the tensor-core sums take up to TC_MMAX columns, the direct FP64 kernel CB_MMAX
+    if (m > (ctx->prm.proj_tc ? TC_MMAX : CB_MMAX)) return DDP_ERR_UNSUPPORTED;
     const DomainDev *d;
     const GaugeDev *g;
     int rc = domain_of(ctx, domain_id, &d, &g);
@@ -741,9 +798,25 @@ int ddp_projected_nucleon(ddp_ctx *ctx, int L0, int m, const double *X, const do
     if ((rc = a.init(ctx, X, xb, true)) || (rc = b.init(ctx, Y, xb, true)) ||
         (rc = c.init(ctx, C_out, (size_t)L0 * L0 * sizeof(double2), false)))
         return rc;
-    k_proj_nucleon<<<L0 * L0, 256, 0, ctx->stream>>>((const double2 *)a.dev, (const double2 *)b.dev, L0, m,
-                                                     (double2 *)c.dev);
-    ctx->launches++;
+    const int64_t nk = 4 * (int64_t)m * m * m;
+    const int ntx = (L0 + NK_TILE - 1) / NK_TILE, ntile = ntx * ntx;
+    // K chunks: about four blocks per SM over all tiles, whole staging steps each
+    int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>(4 * 152 / ntile + 1, (nk + NK_STEP - 1) / NK_STEP));
+    int64_t kchunk = (nk + nchunk - 1) / nchunk;
+    kchunk = ((kchunk + NK_STEP - 1) / NK_STEP) * NK_STEP;
+    nchunk = (nk + kchunk - 1) / kchunk;
+    const size_t db = (size_t)L0 * nk * sizeof(double2), pb = (size_t)nchunk * L0 * L0 * sizeof(double2);
+    Arena &ar = ctx->aux;
+    ar.reset();
+    DDP_CUDA(ctx, ar.reserve(db + pb + 512));
+    double2 *D = (double2 *)ar.take(db);
+    double2 *part = (double2 *)ar.take(pb);
+    const int64_t nd = (int64_t)L0 * nk;
+    k_nucleon_d<<<(unsigned)((nd + 255) / 256), 256, 0, ctx->stream>>>((const double2 *)a.dev, L0, m, D);
+    k_nucleon_gemm<<<dim3((unsigned)nchunk, (unsigned)ntile), NK_TILE * NK_TILE, 0, ctx->stream>>>(
+        (const double2 *)b.dev, D, L0, nk, kchunk, part);
+    k_nucleon_sum<<<(L0 * L0 + 255) / 256, 256, 0, ctx->stream>>>(part, (int)nchunk, L0, (double2 *)c.dev);
+    ctx->launches += 3;
     DDP_CUDA(ctx, cudaGetLastError());
     return c.copy_out();
 }

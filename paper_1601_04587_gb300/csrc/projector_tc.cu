@@ -53,8 +53,10 @@ constexpr int GEMM_BLOCK = GEMM_THREADS;
 constexpr int DCOLS = TN / (GEMM_THREADS / 128);  // accumulator columns a thread drains
 constexpr int TMEM_COLS = 512;  // S * TN = 448 used
 constexpr int MAX_STEPS_PER_BLOCK = 1 << 16;  // keeps the fixed-point sums far below 2^63
-constexpr int ESITES = 16;    // sites per block of the diquark kernel
-constexpr int MMAX = 32;
+constexpr int MMAX = TC_MMAX; // largest number of columns (the paper's 120 modes fit)
+// sites per block of the diquark kernel: all m spinors of the block's sites are staged in
+// shared memory, m * ES * 192 bytes (16 sites up to 32 columns, 4 beyond)
+constexpr int ES_SMALL = 16, ES_LARGE = 4, ES_SMALL_MMAX = 32;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 
 static_assert(S * TN <= TMEM_COLS, "accumulators exceed the tensor memory");
@@ -211,11 +213,24 @@ __device__ __forceinline__ void dfc_mac(float acc[4], float4 a, float4 b, float 
 // largest |Re|, |Im| of s_k(x)_{alpha c} over x and c.
 __global__ void __launch_bounds__(256) k_colour_max(const double2 *A, int64_t n, int64_t site0, int64_t slice_n,
                                                     int m, double *colmax) {
-    __shared__ double bm[128];
+    __shared__ double bm[4 * MMAX];
     const int Q = 4 * m, per = blockDim.x / Q;
     for (int q = threadIdx.x; q < Q; q += blockDim.x) bm[q] = 0;
     __syncthreads();
-    if ((int)threadIdx.x < per * Q) {
+    if (per == 0) {
+        // more columns than threads: each thread takes columns q, q + blockDim.x, ...
+        // over the block's share of the sites
+        for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+            const int k = q / 4, al = q % 4;
+            double mx = 0;
+            for (int64_t x = blockIdx.x; x < slice_n; x += gridDim.x)
+                for (int c = 0; c < 3; c++) {
+                    const double2 v = A[((int64_t)k * n + site0 + x) * 12 + 3 * al + c];
+                    mx = fmax(mx, fmax(mag(v.x), mag(v.y)));
+                }
+            bm[q] = mx;
+        }
+    } else if ((int)threadIdx.x < per * Q) {
         const int q = threadIdx.x % Q, k = q / 4, al = q % 4;
         double mx = 0;
         for (int64_t x = blockIdx.x * (int64_t)per + threadIdx.x / Q; x < slice_n; x += (int64_t)gridDim.x * per)
@@ -246,8 +261,10 @@ struct EArgs {
 
 // The diquarks E^c_ij(x) = i sum over the spin pairs of Eq. W0tbary for i <= j, formed
 // from the spinors scaled by 2^-f_k (so that double-FP32 arithmetic keeps its range),
-// with the row maxima.  Block: ESITES sites, all rows; 16 consecutive threads share a row.
+// with the row maxima.  Block: ESITES sites, all rows; ESITES consecutive threads share a row.
+template <int ESITES>
 __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
+    static_assert(ESITES >= 1 && ESITES <= 32 && (ESITES & (ESITES - 1)) == 0, "row groups within a warp");
     extern __shared__ float4 sh[];  // [m][12][ESITES]: the site index fastest
     __shared__ int fexp[MMAX];
     const int m = a.m;
@@ -296,8 +313,8 @@ __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
                 mx = fmaxf(mx, fmaxf(magf(R.x), magf(I.x)));
             }
         }
-        for (int off = 8; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        if ((threadIdx.x & 15) == 0 && r < a.rows && mx > 0.f) atomic_max_pos(a.rowmax + r, (double)mx);
+        for (int off = ESITES / 2; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if ((threadIdx.x & (ESITES - 1)) == 0 && r < a.rows && mx > 0.f) atomic_max_pos(a.rowmax + r, (double)mx);
     }
 }
 
@@ -454,7 +471,9 @@ __device__ __forceinline__ bool drain_barrier_or(bool v) {
     return r != 0;
 }
 
-// One CTA per (128-row tile, 64-column tile, K range).  Thread 0 streams the operand
+// One CTA per (64-column tile, 128-row tile, K range): the column tiles of one row tile
+// are neighbours in the launch order, so that the CTAs streaming the same A blocks run at
+// the same time and share them through L2.  Thread 0 streams the operand
 // blocks of each K step into NSTAGE buffers (two bulk copies per step) and issues the
 // MMAs; after every CS steps the sixteen warps drain the seven accumulators (warp w: lanes 32 (w % 4) .. + 31, columns DCOLS (w / 4) .. + DCOLS - 1)
 // into exact 64-bit fixed point.
@@ -463,7 +482,7 @@ __global__ void __launch_bounds__(GEMM_BLOCK, 1) k_ozaki_gemm(GemmArgs a) {
     __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE];
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int mt = blockIdx.x, nt = blockIdx.y, z = blockIdx.z;
+    const int nt = blockIdx.x, mt = blockIdx.y, z = blockIdx.z;
     const int s0 = (int)((int64_t)a.KS * z / a.ksplit), s1 = (int)((int64_t)a.KS * (z + 1) / a.ksplit);
     const int nsteps = s1 - s0;
     if (warp == 0) {
@@ -681,9 +700,11 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
     int *rexp = (int *)ar.take((size_t)rows * 4);
     int *cexp = (int *)ar.take((size_t)Q * 4);
     int *err = (int *)ar.take(64);
-    const size_t esm = (size_t)m * ESITES * 12 * sizeof(float4);
+    const int es = m <= ES_SMALL_MMAX ? ES_SMALL : ES_LARGE;
+    const size_t esm = (size_t)m * es * 12 * sizeof(float4);
     const size_t gsm = (size_t)NSTAGE * STAGE;
-    DDP_CUDA(ctx, cudaFuncSetAttribute(k_colour_E, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+    DDP_CUDA(ctx, cudaFuncSetAttribute(es == ES_SMALL ? k_colour_E<ES_SMALL> : k_colour_E<ES_LARGE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
     DDP_CUDA(ctx, cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     cudaStream_t st = ctx->stream;
     DDP_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -704,7 +725,10 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
         ea.colmax = colmax;
         k_colour_max<<<(unsigned)std::min<int64_t>(2 * 152, (slice_n + 1) / 2), 256, 0, st>>>(A, n, site0, slice_n,
                                                                                           m, colmax);
-        k_colour_E<<<(unsigned)((slice_n + ESITES - 1) / ESITES), 256, esm, st>>>(ea);
+        if (es == ES_SMALL)
+            k_colour_E<ES_SMALL><<<(unsigned)((slice_n + ES_SMALL - 1) / ES_SMALL), 256, esm, st>>>(ea);
+        else
+            k_colour_E<ES_LARGE><<<(unsigned)((slice_n + ES_LARGE - 1) / ES_LARGE), 256, esm, st>>>(ea);
         SplitArgs sa;
         sa.E = E;
         sa.A = A;
@@ -737,7 +761,7 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
         g.ncols = ncols;
         g.part = part;
         g.err = err;
-        k_ozaki_gemm<<<dim3(MT, NT, ksplit), GEMM_BLOCK, gsm, st>>>(g);
+        k_ozaki_gemm<<<dim3(NT, MT, ksplit), GEMM_BLOCK, gsm, st>>>(g);
         const int64_t nx = (int64_t)rows * Q;
         k_ozaki_finish<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(
             part, ksplit, prow, ncols, m, rows, rowmax, colmax, X + (int64_t)((o0 + z) % L0) * m * m * Q);
@@ -761,9 +785,10 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
 // G[i][j] = sum_r conj(A_i[r]) A_j[r] over the rows r of one segment, on the same
 // emulated-FP64 product: A' rows i = [Re A_i | Im A_i], B' rows = [Re A_j | Im A_j]
 // (the real parts, columns j < m) and [Im A_j | -Re A_j] (the imaginary parts,
-// m <= c < 2m), every row and column with its own power-of-two exponent.  The m <= 32
+// m <= c < 2m), every row and column with its own power-of-two exponent.  The m <= 128
 // rows of A' are stored as R8 = 8 ceil(m / 8) rows per block (the MMA's other rows read
-// whatever follows in shared memory and feed accumulator rows that are never used).
+// whatever follows in shared memory and feed accumulator rows that are never used); the
+// 2m columns of B' span ceil(2m / 64) column tiles.
 
 namespace {
 
@@ -784,9 +809,9 @@ __global__ void __launch_bounds__(256) k_gram_max(const double2 *A, int64_t cs, 
 struct GramSplitArgs {
     const double2 *A;
     int64_t cs, r0, nrow;  // column stride; the segment's rows
-    int m, R8, KSh;
+    int m, R8, KSh, NT;
     const int *cexp;       // exponents of the columns
-    __nv_bfloat16 *Aq, *Bq;  // [2 KSh][S][R8 x KSTEP], [2 KSh][S][64 x KSTEP]
+    __nv_bfloat16 *Aq, *Bq;  // [2 KSh][S][R8 x KSTEP], [NT][2 KSh][S][64 x KSTEP]
 };
 
 __global__ void k_gram_split_A(GramSplitArgs a) {
@@ -818,11 +843,13 @@ __global__ void k_gram_split_A(GramSplitArgs a) {
 __global__ void k_gram_split_B(GramSplitArgs a) {
     const int tile = TN * KSTEP;
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= (int64_t)a.KSh * tile) return;
+    if (g >= (int64_t)a.NT * a.KSh * tile) return;
     const int e = (int)(g % tile);
-    const int ksr = (int)(g / tile);
+    const int64_t t = g / tile;
+    const int ksr = (int)(t % a.KSh), nt = (int)(t / a.KSh);
     int col, kl;
     tile_pos(e, col, kl);
+    col += nt * TN;
     const int64_t kx = (int64_t)ksr * KSTEP + kl;
     const int j = col < a.m ? col : col - a.m;
     __nv_bfloat16 lo[S], hi[S];
@@ -835,7 +862,9 @@ __global__ void k_gram_split_B(GramSplitArgs a) {
     } else {
         for (int p = 0; p < S; p++) lo[p] = hi[p] = __double2bfloat16(0.0);
     }
-    const int64_t blo = (int64_t)ksr * S, bhi = (int64_t)(a.KSh + ksr) * S;
+    // tile block (nt, K step, slice), as k_ozaki_gemm reads it
+    const int64_t KS = 2 * (int64_t)a.KSh;
+    const int64_t blo = (nt * KS + ksr) * S, bhi = (nt * KS + a.KSh + ksr) * S;
     for (int p = 0; p < S; p++) {
         a.Bq[(blo + p) * tile + e] = lo[p];
         a.Bq[(bhi + p) * tile + e] = hi[p];
@@ -844,13 +873,13 @@ __global__ void k_gram_split_B(GramSplitArgs a) {
 
 // G[i][j] = 2^(e_i + e_j - 14) (sum of the K-range partials of the real and the
 // imaginary column), fixed order.
-__global__ void k_gram_finish(const double *part, int ksplit, int m, const double *colmax, double2 *G) {
+__global__ void k_gram_finish(const double *part, int ksplit, int ncols, int m, const double *colmax, double2 *G) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= m * m) return;
     const int i = g / m, j = g % m;
     double re = 0, im = 0;
     for (int s = 0; s < ksplit; s++) {
-        const double *p = part + ((int64_t)s * TM + i) * TN;
+        const double *p = part + ((int64_t)s * TM + i) * ncols;
         re += p[j];
         im += p[m + j];
     }
@@ -866,18 +895,19 @@ namespace ddp {
 
 // Gram blocks of nseg consecutive row segments of seg rows each on the tensor cores:
 // out[z][i][j] = sum over the rows r of segment z of conj(A_i[r]) A_j[r], A_i[r] the
-// complex component r of column i (column stride cs); A and out on the device, m <= 32.
+// complex component r of column i (column stride cs); A and out on the device, m <= 128.
 int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int nseg, double2 *out) {
-    if (m < 1 || 2 * m > TN) return DDP_ERR_UNSUPPORTED;
+    if (m < 1 || m > TM) return DDP_ERR_UNSUPPORTED;
     const int R8 = 8 * ((m + 7) / 8);
     const int a_bytes = R8 * KSTEP * 2;
+    const int NT = (2 * m + TN - 1) / TN, ncols = NT * TN;
     const int64_t KSh64 = (seg + KSTEP - 1) / KSTEP;
     if (KSh64 > (1 << 28)) return DDP_ERR_UNSUPPORTED;
     const int KSh = (int)KSh64, KS = 2 * KSh;
-    int ksplit = std::max(1, std::min(KS, 152));
+    int ksplit = std::max(1, std::min(KS, 152 / NT));
     ksplit = std::max(ksplit, (KS + MAX_STEPS_PER_BLOCK - 1) / MAX_STEPS_PER_BLOCK);
-    const size_t bA = (size_t)S * KS * a_bytes, bB = (size_t)S * KS * TILE_B;
-    const size_t bP = (size_t)ksplit * TM * TN * sizeof(double);
+    const size_t bA = (size_t)S * KS * a_bytes, bB = (size_t)S * NT * KS * TILE_B;
+    const size_t bP = (size_t)ksplit * TM * ncols * sizeof(double);
     Arena &ar = ctx->aux;
     ar.reset();
     DDP_CUDA(ctx, ar.reserve(bA + bB + bP + (size_t)m * 12 + 64 + 7 * 256));
@@ -904,11 +934,12 @@ int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int 
         sa.m = m;
         sa.R8 = R8;
         sa.KSh = KSh;
+        sa.NT = NT;
         k_exponents<<<(m + 255) / 256, 256, 0, st>>>(colmax, m, cexp);
         sa.cexp = cexp;
         sa.Aq = (__nv_bfloat16 *)Aq;
         sa.Bq = (__nv_bfloat16 *)Bq;
-        const int64_t na = (int64_t)KSh * R8 * KSTEP, nb = (int64_t)KSh * TN * KSTEP;
+        const int64_t na = (int64_t)KSh * R8 * KSTEP, nb = (int64_t)NT * KSh * TN * KSTEP;
         k_gram_split_A<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(sa);
         k_gram_split_B<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(sa);
         GemmArgs g;
@@ -916,14 +947,14 @@ int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int 
         g.Bq = Bq;
         g.a_bytes = a_bytes;
         g.MT = 1;
-        g.NT = 1;
+        g.NT = NT;
         g.KS = KS;
         g.ksplit = ksplit;
-        g.ncols = TN;
+        g.ncols = ncols;
         g.part = part;
         g.err = err;
-        k_ozaki_gemm<<<dim3(1, 1, ksplit), GEMM_BLOCK, gsm, st>>>(g);
-        k_gram_finish<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(part, ksplit, m, colmax,
+        k_ozaki_gemm<<<dim3(NT, 1, ksplit), GEMM_BLOCK, gsm, st>>>(g);
+        k_gram_finish<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(part, ksplit, ncols, m, colmax,
                                                                        out + (int64_t)z * m * m);
         ctx->launches += 6;
         DDP_CUDA(ctx, cudaGetLastError());

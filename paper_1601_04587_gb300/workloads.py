@@ -238,7 +238,7 @@ def next_rows_workload(ddp, torch, ctx, synth, precision, steps=2, warmup=1, L=N
 
 # ------------------------------------------------ projector-cut factorization
 
-def projector_workload(ddp, torch, ctx, synth, precision, nm=24, iters=10, steps=1, warmup=1, L=None, x0_cut=24,
+def projector_workload(ddp, torch, ctx, synth, precision, nm=120, iters=10, steps=1, warmup=1, L=None, x0_cut=24,
                        delta=8):
     """48 x 24^3 lattice, kappa 0.140, the projector cut of Sec. 5 at x0_cut = 24 with
     Delta = 8: Gamma-bar_0 = time slices [0, 32), Gamma*_0 = [24, 48), Omega = [16, 32).

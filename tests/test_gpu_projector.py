@@ -232,13 +232,83 @@ def test_colourless_tensor_cores_full_slice(ddp):
 
 
 def test_colourless_slices_rejects_too_many_columns(ddp, env):
+    """More than 128 columns on the tensor cores, more than 32 with the direct FP64 kernel."""
     U, ctx, doms = env
     n = oracle.box_sites(OMEGA[1])
-    A = torch.zeros((33, n, 4, 3), dtype=torch.complex128, device="cuda")
     X = torch.zeros(1, dtype=torch.complex128, device="cuda")
-    with pytest.raises(ddp.DDPError) as ei:
-        ddp.ddp_colourless_slices(ctx, doms["omega"], A, 33, 0, X)
-    assert ei.value.status == ddp.DDP_ERR_UNSUPPORTED
+    for m, tc in ((129, 1), (33, 0)):
+        A = torch.zeros((m, n, 4, 3), dtype=torch.complex128, device="cuda")
+        with _Path(ddp, ctx, tc):
+            with pytest.raises(ddp.DDPError) as ei:
+                ddp.ddp_colourless_slices(ctx, doms["omega"], A, m, 0, X)
+        assert ei.value.status == ddp.DDP_ERR_UNSUPPORTED
+
+
+def test_colourless_tensor_cores_paper_modes(ddp):
+    """N_m = 120 columns, the number of modes of the paper's projector (Sec. 5): 7260
+    diquark rows (57 row tiles), 960 output columns (15 column tiles), on a 2 x 4^3
+    lattice, against the oracle."""
+    L2 = (2, 4, 4, 4)
+    box = ((0, 0, 0, 0), L2)
+    m = 120
+    ctx = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        U = synth.gauge_field(L2, seed=45)
+        gid = ddp.ddp_load_gauge(ctx, torch.from_numpy(U).cuda(), L2, ddp.DDP_BC_PERIODIC)
+        did = ddp.ddp_set_domain(ctx, gid, *box)
+        A = synth.random_spinor(m, oracle.box_sites(box[1]), 92)
+        X = torch.zeros((L2[0], m, m, m, 4), dtype=torch.complex128, device="cuda")
+        ddp.ddp_colourless_slices(ctx, did, _dev(A), m, 2, X)
+        got = X.cpu().numpy()
+        del X
+    finally:
+        ddp.ddp_destroy(ctx)
+    assert _rel(got, projector.colourless_spinors(L2, *box, _forms(A, 2))) < TC_TOL
+
+
+@pytest.mark.parametrize("m,form,box", [(40, 1, ((1, 0, 0, 0), (2, 8, 8, 8))),
+                                        (33, 0, ((5, 0, 0, 0), (2, 8, 8, 8)))])
+def test_colourless_tensor_cores_more_than_32_columns(ddp, env8, m, form, box):
+    """Beyond 32 columns (4 sites per diquark block, column maxima with more columns
+    than threads), on 512-site slices, the second box wrapping in time."""
+    ctx, gid = env8
+    did = ddp.ddp_set_domain(ctx, gid, *box)
+    A = synth.random_spinor(m, oracle.box_sites(box[1]), 150 + m)
+    X = torch.zeros((L8[0], m, m, m, 4), dtype=torch.complex128, device="cuda")
+    ddp.ddp_colourless_slices(ctx, did, _dev(A), m, form, X)
+    ddp.ddp_free_domain(ctx, did)
+    got = X.cpu().numpy()
+    assert _rel(got, projector.colourless_spinors(L8, *box, _forms(A, form))) < TC_TOL
+    inside = np.zeros(L8[0], bool)
+    inside[[(box[0][0] + t) % L8[0] for t in range(box[1][0])]] = True
+    assert not np.any(got[~inside])
+
+
+@pytest.mark.parametrize("L0,m", [(12, 5), (20, 7), (3, 40)])
+def test_projected_nucleon_matches_oracle(ddp, env, L0, m):
+    """The nucleon projection as a product over the 4 m^3 (i, j, k, alpha) terms against
+    the oracle's contraction, on random X and Y: time extents inside one 16 x 16 output
+    tile, across tiles with ragged edges, and m > 32."""
+    U, ctx, doms = env
+    rng = np.random.default_rng(300 + m)
+    shape = (L0, m, m, m, 4)
+    X = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    Y = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    C = torch.zeros((L0, L0), dtype=torch.complex128, device="cuda")
+    ddp.ddp_projected_nucleon(ctx, L0, m, _dev(X), _dev(Y), C)
+    assert _rel(C.cpu().numpy(), projector.projected_nucleon(X, Y)) < 1e-12
+
+
+def test_orthonormalize_more_than_32_columns(ddp, env):
+    """40 columns: the Gram blocks over two tensor-core column tiles and the double-FP32
+    update with R^-1 staged a column tile at a time."""
+    U, ctx, doms = env
+    n = oracle.box_sites(OMEGA[1])
+    m = 40
+    V = synth.random_spinor(m, n, 4)
+    Vd = _dev(V)
+    ddp.ddp_orthonormalize(ctx, doms["omega"], Vd, m)
+    assert np.abs(Vd.cpu().numpy() - projector.orthonormalize(V)).max() < 1e-12
 
 
 def test_projected_pion_and_nucleon_pipeline(ddp, env):
@@ -323,10 +393,14 @@ def test_colourless_nan_input_stays_local(ddp, env8, tc):
 
 @pytest.mark.parametrize("m,box", [(1, ((0, 0, 0, 0), (3, 8, 8, 8))),
                                    (20, ((1, 0, 0, 0), (2, 8, 8, 8))),
-                                   (32, ((4, 0, 0, 0), (3, 8, 8, 8)))])
+                                   (32, ((4, 0, 0, 0), (3, 8, 8, 8))),
+                                   (40, ((2, 0, 0, 0), (2, 8, 8, 8))),
+                                   (120, ((5, 0, 0, 0), (2, 8, 8, 8))),
+                                   (128, ((0, 0, 0, 0), (1, 8, 8, 8)))])
 def test_gram_tensor_cores_sizes(ddp, env8, m, box):
-    """m = 1, 20 and 32 (the largest) columns over 512-site slices, the last box wrapping
-    in time; both paths against the oracle, slices outside the box zero."""
+    """m = 1 to 128 (the largest; 120 is the paper's number of modes) columns over
+    512-site slices, one to four 64-column tiles, a box wrapping in time; both paths
+    against the oracle, slices outside the box zero."""
     ctx, gid = env8
     did = ddp.ddp_set_domain(ctx, gid, *box)
     A = synth.random_spinor(m, oracle.box_sites(box[1]), 60 + m)
