@@ -399,7 +399,9 @@ int ddp_gram_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, double 
  * of Eq. W0tbary (C = i g0 g2) with s_i = A_i (form 0), g5 conj(A_i) (form 1: the
  * spinor of the row phi_i^+ D^-1 when A_i = D^-1 g5 phi_i) or -A_i (form 2).
  * X_out: L0 x m^3 x 4 complex.  m <= 128 on the tensor cores, m <= 32 with the direct
- * FP64 kernel (else DDP_ERR_UNSUPPORTED). */
+ * FP64 kernel (else DDP_ERR_UNSUPPORTED).  The tensor-core sums need scratch of about
+ * (66 m^2 + 700 m) bytes per site of a time slice (14.5 GB at m = 120 on a 24^3 slice),
+ * which the context keeps for later calls until ddp_destroy. */
 int ddp_colourless_slices(ddp_ctx *ctx, int domain_id, const double *A, int m, int form, double *X_out);
 
 /* C[y0][x0] = (1/L^3) sum_ij Mt[y0][i][j] M[x0][j][i] = (1/L^3) sum_{x vec, y vec} W~(y, x)

@@ -311,12 +311,14 @@ def test_orthonormalize_more_than_32_columns(ddp, env):
     assert np.abs(Vd.cpu().numpy() - projector.orthonormalize(V)).max() < 1e-12
 
 
-def test_projected_pion_and_nucleon_pipeline(ddp, env):
+@pytest.mark.parametrize("m", [6, 48])
+def test_projected_pion_and_nucleon_pipeline(ddp, env, m):
     """Modes on Omega, u_i = D^-1_{Gbar} g5 phi_i, w_i = D^-1_{G*} sigma_i, the pion
     from the Gram blocks and the nucleon from the colourless spinors, all on the GPU,
-    against the oracle's route."""
+    against the oracle's route; m = 48 takes every path beyond 32 modes (Gram blocks over
+    two column tiles, the tiled Cholesky-QR update, 4-site diquark blocks, the nucleon
+    product over 4 m^3 terms)."""
     U, ctx, doms = env
-    m = 6
     n_o, n_b, n_s = (oracle.box_sites(b[1]) for b in (OMEGA, GBAR, GSTAR))
     V0 = synth.random_spinor(m, n_o, 21)
     phi = projector.inverse_iteration(U, L, AP, *OMEGA, KAPPA, V0, 2)
