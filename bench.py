@@ -590,6 +590,46 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_colourless(args):
+    """The colourless-spinor sums of the projector cut (Eq. W0tbary) on one 24^3 time slice
+    with --modes spinor columns (random, seeded, device-resident), the size of every slice
+    of the 48x24^3 projector workload: CUDA-event time per call (diquarks, splitting,
+    the emulated-FP64 tensor-core product, exponents and symmetric fill) and the rate of
+    the slice-pair MMA work that the product issues."""
+    import torch
+
+    import paper_1601_04587_gb300 as ddp
+
+    m = args.modes
+    Ls = (2, 24, 24, 24)
+    box = ((0, 0, 0, 0), (1, 24, 24, 24))
+    ns = 24 ** 3
+    ctx = ddp.ddp_create(0, torch.cuda.current_stream().cuda_stream)
+    U = synth.gauge_field_torch(Ls, seed=synth.SEED_GAUGE, device="cuda")
+    gid = ddp.ddp_load_gauge(ctx, U, Ls, ddp.DDP_BC_ANTIPERIODIC)
+    did = ddp.ddp_set_domain(ctx, gid, *box)
+    A = torch.from_numpy(synth.random_spinor(m, ns, synth.SEED_NOISE0 + 11)).cuda()
+    X = torch.zeros((Ls[0], m, m, m, 4), dtype=torch.complex128, device="cuda")
+    ddp.ddp_colourless_slices(ctx, did, A, m, 1, X)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.iters):
+        ddp.ddp_colourless_slices(ctx, did, A, m, 1, X)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.iters
+    ddp.ddp_destroy(ctx)
+    rows, q = m * (m + 1) // 2, 4 * m
+    mt, nt = -(-rows // 128), -(-(2 * q) // 64)
+    kp = -(-(2 * 3 * ns) // 16) * 16  # [Re | Im] halves of the 3 x sites reduction, 16-deep steps
+    mma_flop = 28 * 2.0 * (mt * 128) * (nt * 64) * kp  # 28 slice-pair products per padded tile
+    fp64_flop = 8.0 * rows * q * 3 * ns  # the complex product itself, one multiply-add = 8 flops
+    print(json.dumps({"workload": "colourless", "slice": [24, 24, 24], "modes": m, "diquark_rows": rows,
+                      "tiles": [mt, nt], "ms_per_slice": ms, "mma_tflops": mma_flop / ms / 1e9,
+                      "fp64_equivalent_tflops": fp64_flop / ms / 1e9}))
+
+
 def run_hop(args):
     """One stencil variant alone on a whole lattice (the ncu target for the stencil
     profiles): average CUDA-event time of `--iters` launches and the bandwidth its
@@ -629,16 +669,17 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--workload", default="slabs", choices=["slabs", "batch", "multilevel", "serve", "next", "hop",
-                                                         "projector"],
+                                                         "projector", "colourless"],
                     help="slabs: the benchmark line; the others print their own measurement line")
     ap.add_argument("--lattice", type=int, nargs=4, default=[32, 24, 24, 24], help="--workload hop: lattice")
     ap.add_argument("--kernel", default="all", help="--workload hop: plain, schur_rhat, schur_ts or all")
     ap.add_argument("--ncol", type=int, default=12, help="--workload hop: columns")
-    ap.add_argument("--iters", type=int, default=20, help="--workload hop: timed launches per kernel")
+    ap.add_argument("--iters", type=int, default=20,
+                    help="--workload hop: timed launches per kernel; colourless: timed calls")
     ap.add_argument("--param", action="append", default=[],
                     help="solver parameter name=value passed to ddp_set_param (repeatable)")
     ap.add_argument("--modes", type=int, default=120,
-                    help="--workload projector: number of modes N_m (default 120, the paper's)")
+                    help="--workload projector / colourless: number of modes N_m (default 120, the paper's)")
     ap.add_argument("--kappa", type=float, default=None, help="slabs: kappa (default 0.14)")
     ap.add_argument("--csw", type=float, default=0.0, help="slabs: clover coefficient c_sw (default 0)")
     ap.add_argument("--no-conditional", action="store_true",
@@ -665,6 +706,8 @@ def main():
         run_reference(args)
     elif args.workload == "hop":
         run_hop(args)
+    elif args.workload == "colourless":
+        run_colourless(args)
     elif args.workload != "slabs":
         run_other(args)
     else:

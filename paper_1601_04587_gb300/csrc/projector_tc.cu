@@ -55,8 +55,11 @@ constexpr int TMEM_COLS = 512;  // S * TN = 448 used
 constexpr int MAX_STEPS_PER_BLOCK = 1 << 16;  // keeps the fixed-point sums far below 2^63
 constexpr int MMAX = TC_MMAX; // largest number of columns (the paper's 120 modes fit)
 // sites per block of the diquark kernel: all m spinors of the block's sites are staged in
-// shared memory, m * ES * 192 bytes (16 sites up to 32 columns, 4 beyond)
+// shared memory, m * ES * 192 bytes (16 sites up to 32 columns, 4 beyond, plus 64 bytes
+// of padding per column)
 constexpr int ES_SMALL = 16, ES_LARGE = 4, ES_SMALL_MMAX = 32;
+// float4 elements between the staged spinors of consecutive columns k
+__host__ __device__ constexpr int colour_kstride(int es) { return 12 * es + (es == 4 ? 4 : 0); }
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 
 static_assert(S * TN <= TMEM_COLS, "accumulators exceed the tensor memory");
@@ -265,7 +268,10 @@ struct EArgs {
 template <int ESITES>
 __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
     static_assert(ESITES >= 1 && ESITES <= 32 && (ESITES & (ESITES - 1)) == 0, "row groups within a warp");
-    extern __shared__ float4 sh[];  // [m][12][ESITES]: the site index fastest
+    // [m][12][ESITES] with the site index fastest; with 4 sites the spinors of consecutive
+    // k start 16 banks apart, so that the two rows a quarter-warp reads do not collide
+    constexpr int KSTR = colour_kstride(ESITES);
+    extern __shared__ float4 sh[];
     __shared__ int fexp[MMAX];
     const int m = a.m;
     const int64_t x0 = (int64_t)blockIdx.x * ESITES;
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
             re = make_float2(-re.x, -re.y);
             im = make_float2(-im.x, -im.y);
         }
-        sh[(k * 12 + c) * ESITES + xs] = make_float4(re.x, re.y, im.x, im.y);
+        sh[k * KSTR + c * ESITES + xs] = make_float4(re.x, re.y, im.x, im.y);
     }
     __syncthreads();
     const int nit = a.rows * ESITES;
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(256) k_colour_E(EArgs a) {
         if (r < a.rows && xs < ns) {
             int i, j;
             pair_of(r, m, i, j);
-            const float4 *si = sh + i * 12 * ESITES + xs, *sj = sh + j * 12 * ESITES + xs;
+            const float4 *si = sh + i * KSTR + xs, *sj = sh + j * KSTR + xs;
             float4 *o = a.E + (int64_t)r * 3 * a.slice_n + (x0 + xs) * 3;
             for (int c = 0; c < 3; c++) {
                 const int ca = (c + 1) % 3, cb = (c + 2) % 3;
@@ -640,6 +646,22 @@ __global__ void __launch_bounds__(GEMM_BLOCK, 1) k_ozaki_gemm(GemmArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS) : "memory");
 }
 
+// Number of K ranges per output tile.  The product runs one CTA per SM: up to one wave,
+// as many ranges as fill it; where that leaves the last wave poorly filled (few tiles
+// per wave, or a ragged tail), more ranges of at least 8 chunks each are taken if they
+// fill the waves better by more than 5%.  Every range stays below MAX_STEPS_PER_BLOCK.
+int pick_ksplit(int tiles, int KS) {
+    constexpr int NSM = 152;
+    auto fill = [&](int k) {
+        const int64_t ctas = (int64_t)tiles * k;
+        return (double)ctas / (double)(((ctas + NSM - 1) / NSM) * NSM);
+    };
+    int best = std::max(1, std::min(KS, NSM / tiles));
+    for (int k = best + 1; k <= 256 && k <= KS / (8 * CS); k++)
+        if (fill(k) > fill(best) + 0.05) best = k;
+    return std::max(best, (KS + MAX_STEPS_PER_BLOCK - 1) / MAX_STEPS_PER_BLOCK);
+}
+
 // X[i][j][k][alpha] = X[j][i][k][alpha] = 2^(e_row + e_col - 14) sum over the K-range
 // partials (fixed order).
 __global__ void k_ozaki_finish(const double *part, int ksplit, int prow, int ncols, int m, int rows,
@@ -682,8 +704,7 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
     const int64_t KSh64 = (K + KSTEP - 1) / KSTEP;
     if (KSh64 > (1 << 28)) return DDP_ERR_UNSUPPORTED;
     const int KSh = (int)KSh64, KS = 2 * KSh;
-    int ksplit = std::max(1, std::min(KS, 152 / (MT * NT)));
-    ksplit = std::max(ksplit, (KS + MAX_STEPS_PER_BLOCK - 1) / MAX_STEPS_PER_BLOCK);
+    const int ksplit = pick_ksplit(MT * NT, KS);
     const int ncols = NT * TN, prow = MT * TM;
     const size_t bE = (size_t)rows * K * sizeof(float4);
     const size_t bA = (size_t)S * MT * KS * TILE_A, bB = (size_t)S * NT * KS * TILE_B;
@@ -701,7 +722,7 @@ int colourless_tc(ddp_ctx *ctx, const double2 *A, int64_t n, int m, int form, in
     int *cexp = (int *)ar.take((size_t)Q * 4);
     int *err = (int *)ar.take(64);
     const int es = m <= ES_SMALL_MMAX ? ES_SMALL : ES_LARGE;
-    const size_t esm = (size_t)m * es * 12 * sizeof(float4);
+    const size_t esm = (size_t)m * colour_kstride(es) * sizeof(float4);
     const size_t gsm = (size_t)NSTAGE * STAGE;
     DDP_CUDA(ctx, cudaFuncSetAttribute(es == ES_SMALL ? k_colour_E<ES_SMALL> : k_colour_E<ES_LARGE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
@@ -904,8 +925,7 @@ int gram_tc(ddp_ctx *ctx, const double2 *A, int64_t cs, int m, int64_t seg, int 
     const int64_t KSh64 = (seg + KSTEP - 1) / KSTEP;
     if (KSh64 > (1 << 28)) return DDP_ERR_UNSUPPORTED;
     const int KSh = (int)KSh64, KS = 2 * KSh;
-    int ksplit = std::max(1, std::min(KS, 152 / NT));
-    ksplit = std::max(ksplit, (KS + MAX_STEPS_PER_BLOCK - 1) / MAX_STEPS_PER_BLOCK);
+    const int ksplit = pick_ksplit(NT, KS);
     const size_t bA = (size_t)S * KS * a_bytes, bB = (size_t)S * NT * KS * TILE_B;
     const size_t bP = (size_t)ksplit * TM * ncols * sizeof(double);
     Arena &ar = ctx->aux;
