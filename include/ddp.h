@@ -310,8 +310,10 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * "projector_tensor_cores" (1, the default: the Gram blocks and colourless
  * spinor sums of the projector cut, m <= 32, run as an emulated-FP64 product on the
  * tensor cores and the Cholesky-QR update A <- A R^-1 in double-FP32; 0: direct FP64
- * kernels).  DDP_ERR_INVALID_ARG for unknown names or
- * values. */
+ * kernels), "overlap_downloads" (1, the default: ddp_propagator_series with host
+ * outputs solves the smaller nested domains first and copies their results to the host
+ * while the largest domain solves; 0: one batched solve, then the copies).
+ * DDP_ERR_INVALID_ARG for unknown names or values. */
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value);
 
 /* Inner-loop stencil variants, for ddp_time_hop: one BiCGStab iteration on the

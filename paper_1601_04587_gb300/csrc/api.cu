@@ -1068,7 +1068,7 @@ int ddp_propagator_series(ddp_ctx *ctx, int n, const int *domain_ids, double kap
     // result does not depend on the batch it is solved in.
     bool host_out = false;
     for (int i = 0; i < n; i++) host_out = host_out || s_host[i] || t_host[i];
-    const int first = (host_out && n > 1) ? n - 1 : n;
+    const int first = (host_out && n > 1 && ctx->prm.overlap_downloads) ? n - 1 : n;
     auto combine = [](int a, int b) {
         if (a != DDP_OK && a != DDP_ERR_NOT_CONVERGED) return a;
         if (b != DDP_OK && b != DDP_ERR_NOT_CONVERGED) return b;
@@ -1159,7 +1159,8 @@ int ddp_boundary_source(ddp_ctx *ctx, int domain_from, const double *psi, int do
 }
 
 // Tuning knobs of the solver (names: max_outer, max_inner, delta_fp32,
-// delta_fp16, delta_bf16, delta_fp64, tile_sites, tile_cols, conditional, stencil_carveout, projector_tensor_cores, contraction_double_fp32).
+// delta_fp16, delta_bf16, delta_fp64, tile_sites, tile_cols, conditional, stencil_carveout, projector_tensor_cores, contraction_double_fp32,
+// overlap_downloads).
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
     if (!ctx || !name) return DDP_ERR_INVALID_ARG;
     EngineParams &p = ctx->prm;
@@ -1178,6 +1179,7 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
     } else if (n == "conditional") p.use_conditional = value != 0;
     else if (n == "projector_tensor_cores") p.proj_tc = value != 0;
     else if (n == "contraction_double_fp32") p.contract_dd = value != 0;
+    else if (n == "overlap_downloads") p.overlap_downloads = value != 0;
     else if (n == "stencil_carveout") {
         if (value < -1 || value > 100) return DDP_ERR_INVALID_ARG;
         p.carveout = (int)value;

@@ -86,6 +86,9 @@ struct EngineParams {
     int carveout = 28;
     int contract_dd = 1;        // nucleon contraction in double-FP32 arithmetic (0: FP64)
     int proj_tc = 1;            // projector-cut Gram blocks and colourless sums on the tensor cores (0: FP64 kernels)
+    // ddp_propagator_series with host outputs: solve the smaller nested domains first and
+    // download their results while the largest solves (0: one batched solve, then downloads)
+    int overlap_downloads = 1;
 };
 
 // A growable device arena owned by the context.
