@@ -517,12 +517,15 @@ def test_zero_source_and_bad_kappa(ddp, ctx, field):
 
 # ------------------------------------------------- nested propagators in one call
 
-@pytest.mark.parametrize("where", ["device", "pinned", "numpy"])
-def test_propagator_series_matches_separate_calls(ddp, ctx, field, where):
+@pytest.mark.parametrize("where,overlap", [("device", 1), ("pinned", 1), ("numpy", 1), ("pinned", 0)])
+def test_propagator_series_matches_separate_calls(ddp, ctx, field, where, overlap):
     """ddp_propagator_series gives the same bits as ddp_solve_batch + ddp_series_terms +
     ddp_contract on the same nested domains, whether its outputs are device memory,
-    pinned host memory or plain numpy arrays; the propagators also match the oracle."""
+    pinned host memory or plain numpy arrays, and with host outputs whether the smaller
+    domains are solved first (overlap_downloads 1) or all in one batch (0); the
+    propagators also match the oracle."""
     U, gid = field
+    ddp.ddp_set_param(ctx, "overlap_downloads", overlap)
     src, kappa = (7, 1, 2, 3), 0.124
     boxes = [((6, 0, 0, 0), (4, 4, 4, 6)), ((5, 0, 0, 0), (6, 4, 4, 6)), ((0, 0, 0, 0), LAT)]
     dids = [ddp.ddp_set_domain(ctx, gid, *b) for b in boxes]
@@ -568,6 +571,7 @@ def test_propagator_series_matches_separate_calls(ddp, ctx, field, where):
         for k in (ddp.DDP_CONTRACT_PSEUDO_LOCAL, ddp.DDP_CONTRACT_NUCLEON, ddp.DDP_CONTRACT_PION):
             n = 2 if k == ddp.DDP_CONTRACT_PSEUDO_LOCAL else 2 * LAT[0]
             assert np.array_equal(Cg[i, k, :n], C[i, k, :n]), (i, k)
+    ddp.ddp_set_param(ctx, "overlap_downloads", 1)
     ref, *_ = oracle.propagator(U, LAT, AP, *boxes[0], kappa, src)
     assert max(_col_errors(host(S2[0]), ref)) < 1e-8
     for d in dids:
