@@ -91,9 +91,9 @@ HOP_TRAFFIC_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_
                        "l1tex__m_xbar2l1tex_read_bytes.sum,launch__registers_per_thread")
 
 
-def write_hop_traffic(csv_path):
-    """profiles/hop_traffic.json from the ncu CSV of the three FP32 stencils on the
-    32x24^3 lattice (the --workload hop run with --iters 1 under
+def write_hop_traffic(csv_path, out_path=None):
+    """profiles/hop_traffic.json (or out_path) from the ncu CSV of the three FP32 stencils
+    on the 32x24^3 lattice (the --workload hop run with --iters 1 under
     `ncu --metrics HOP_TRAFFIC_METRICS --clock-control none -k regex:k_hop --csv`):
     DRAM bytes per launch, scaled by site-columns to the 48x24^3 bench launch."""
     import csv
@@ -129,9 +129,10 @@ def write_hop_traffic(csv_path):
                       "plain,schur_rhat,schur_ts --iters 1 (under ncu --metrics " + HOP_TRAFFIC_METRICS +
                       " --clock-control none -k regex:k_hop --csv), then python bench.py --write-hop-traffic CSV",
            "sources_sha256": _stencil_sources_sha256()}
-    with open(os.path.join(ROOT, "profiles", "hop_traffic.json"), "w") as f:
+    with open(out_path or os.path.join(ROOT, "profiles", "hop_traffic.json"), "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps(rec))
+    return rec
 
 
 class ClockSampler:
