@@ -54,6 +54,9 @@ def boxes():
     return out
 
 
+NOMINAL_HBM_GBPS = 7900.0  # GB300 HBM3e, nominal
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -383,7 +386,9 @@ def stencil_roofline(ddp, ctx, U_dev, prec, precision_name, iters=50):
             traffic = rec.get("kernels", {}).get(f"{precision_name}/{name}")
         per[name] = {"computes": what, "launches_per_iteration": per_iter, "ms_per_launch": ms,
                      "algorithmic_bytes_per_launch": nbytes, "achieved": achieved, "frac": achieved / peak,
-                     "traffic": traffic}
+                     "traffic": traffic,
+                     # the ncu DRAM bytes of a launch over its CUDA-event time
+                     "dram_gbps": (traffic / (ms * 1e-3) / 1e9) if traffic else None}
     ddp.ddp_free_domain(ctx, did)
     ddp.ddp_free_gauge(ctx, gid)
     tot = sum(v["launches_per_iteration"] * v["ms_per_launch"] for v in per.values())
@@ -395,7 +400,8 @@ def stencil_roofline(ddp, ctx, U_dev, prec, precision_name, iters=50):
             "traffic": d["traffic"], "kernel": f"k_hop<{precision_name}> {dom}: {d['computes']}",
             "ms_per_launch": d["ms_per_launch"], "algorithmic_bytes_per_launch": d["algorithmic_bytes_per_launch"],
             "launch": "48x24^3 full lattice, 12 columns, 3,981,312 output site-columns",
-            "peak_kind": f"{peak_kind} HBM copy bandwidth", "per_kernel": per}
+            "peak_kind": f"{peak_kind} HBM copy bandwidth", "dram_gbps": d["dram_gbps"],
+            "frac_of_nominal": d["achieved"] / NOMINAL_HBM_GBPS, "nominal_peak": NOMINAL_HBM_GBPS, "per_kernel": per}
 
 
 def run_gpu(args):
