@@ -301,7 +301,9 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * "delta_fp16" / "delta_bf16" (smallest inner relative tolerance per storage
  * format), "tile_sites" (sites per block tile: 32; 0 = automatic),
  * "tile_cols" (columns per block, 1..12, 0 = automatic), "tuned_cols_fp64" ...
- * "tuned_cols_bf16" (a remembered autotuner choice, 0 = none), "conditional" (1: the
+ * "tuned_cols_bf16" (a remembered autotuner choice, 0 = none), "tuned_carveout_fp64" ...
+ * "tuned_carveout_bf16" (the autotuner's stencil carveout for that storage format,
+ * percent, -1 = the driver's choice, -2 = none: "stencil_carveout" applies), "conditional" (1: the
  * inner loop is a device-driven CUDA-graph WHILE node; 0: host-polled graph
  * chunks), "stencil_carveout" (preferred shared-memory share of the unified L1 /
  * shared memory for the inner-loop stencils, percent; default 28, -1 = the driver's
@@ -315,6 +317,11 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * while the largest domain solves; 0: one batched solve, then the copies).
  * DDP_ERR_INVALID_ARG for unknown names or values. */
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value);
+
+/* *value = the current value of a parameter ddp_set_param accepts ("delta_fp64" ...
+ * "delta_bf16" for the inner tolerance floors).  DDP_ERR_INVALID_ARG for unknown
+ * names. */
+int ddp_get_param(const ddp_ctx *ctx, const char *name, double *value);
 
 /* Inner-loop stencil variants, for ddp_time_hop: one BiCGStab iteration on the
  * even-odd Schur complement runs PLAIN twice and each SCHUR variant once. */
@@ -337,10 +344,13 @@ int ddp_time_hop(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precis
 
 /* Autotuner: times the three inner-loop stencil variants on the domain (ncol
  * columns, the given storage format, iters launches each) for every admissible
- * number of columns per thread block, keeps the choice with the shortest
- * stencil time per BiCGStab iteration (2 x PLAIN + SCHUR_RHAT + SCHUR_TS) for
- * that storage format in the context (used by every later solve with that
- * format) and returns it with that time. */
+ * number of columns per thread block (the block shape, 32 sites x columns) and
+ * every candidate shared-memory carveout of the stencils (28, 50, 100 percent of the
+ * unified L1 / shared memory), keeps the pair with the shortest stencil time per
+ * BiCGStab iteration (2 x PLAIN + SCHUR_RHAT + SCHUR_TS) for that storage format in
+ * the context (used by every later solve with that format; ddp_get_param
+ * "tuned_cols_<format>" and "tuned_carveout_<format>" read it back) and returns the
+ * columns with that time. */
 int ddp_autotune(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters, int *best_cols,
                  float *best_ms);
 

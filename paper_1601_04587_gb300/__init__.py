@@ -89,6 +89,7 @@ def lib():
             "ddp_poll": ([vp, ctypes.c_uint64, i4, ctypes.POINTER(ddp_solve_info)], i),
             "ddp_serve_reset": ([vp], i),
             "ddp_set_param": ([vp, ctypes.c_char_p, d], i),
+            "ddp_get_param": ([vp, ctypes.c_char_p, ctypes.POINTER(d)], i),
             "ddp_time_hop": ([vp, i, d, i, i, i, i, ctypes.POINTER(ctypes.c_float),
                               ctypes.POINTER(ctypes.c_double)], i),
             "ddp_kernel_launches": ([vp], ctypes.c_long),
@@ -357,6 +358,12 @@ def ddp_set_param(ctx, name: str, value: float):
     return _check(ctx, lib().ddp_set_param(ctx, name.encode(), float(value)), "ddp_set_param")
 
 
+def ddp_get_param(ctx, name: str) -> float:
+    v = ctypes.c_double(0.0)
+    _check(ctx, lib().ddp_get_param(ctx, name.encode(), ctypes.byref(v)), "ddp_get_param")
+    return v.value
+
+
 def ddp_time_hop(ctx, domain_id, kappa, ncol, precision, iters, kernel=DDP_HOP_PLAIN):
     """(ms per launch, algorithmic bytes per launch) of one inner-loop stencil variant."""
     ms = ctypes.c_float()
@@ -388,12 +395,15 @@ def autotune_cached(ctx, domain_id, n_sites, kappa, ncol, precision, cache_path=
     if path and os.path.exists(path):
         with open(path) as f:
             cache = json.load(f)
+    name = _PREC_NAMES[int(precision)]
     if key in cache:
-        ddp_set_param(ctx, f"tuned_cols_{_PREC_NAMES[int(precision)]}", cache[key]["cols"])
+        ddp_set_param(ctx, f"tuned_cols_{name}", cache[key]["cols"])
+        if "carveout" in cache[key]:
+            ddp_set_param(ctx, f"tuned_carveout_{name}", cache[key]["carveout"])
         return cache[key]["cols"], cache[key]["ms"]
     cols, ms = ddp_autotune(ctx, domain_id, kappa, ncol, precision, iters)
     if path:
-        cache[key] = {"cols": cols, "ms": ms}
+        cache[key] = {"cols": cols, "carveout": int(ddp_get_param(ctx, f"tuned_carveout_{name}")), "ms": ms}
         with open(path, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)
     return cols, ms

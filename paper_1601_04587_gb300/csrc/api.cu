@@ -1158,9 +1158,17 @@ int ddp_boundary_source(ddp_ctx *ctx, int domain_from, const double *psi, int do
     return DDP_OK;
 }
 
+// Storage-format index of a "<name>_fp64" ... "<name>_bf16" parameter, or -1.
+static int prec_suffix(const std::string &n, const char *stem) {
+    static const char *suf[4] = {"_fp64", "_fp32", "_fp16", "_bf16"};
+    for (int k = 0; k < 4; k++)
+        if (n == std::string(stem) + suf[k]) return k;
+    return -1;
+}
+
 // Tuning knobs of the solver (names: max_outer, max_inner, delta_fp32,
 // delta_fp16, delta_bf16, delta_fp64, tile_sites, tile_cols, conditional, stencil_carveout, projector_tensor_cores, contraction_double_fp32,
-// overlap_downloads).
+// overlap_downloads, tuned_cols_*, tuned_carveout_*).
 int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
     if (!ctx || !name) return DDP_ERR_INVALID_ARG;
     EngineParams &p = ctx->prm;
@@ -1189,6 +1197,30 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
         int k = n == "tuned_cols_fp64" ? 0 : n == "tuned_cols_fp32" ? 1 : n == "tuned_cols_fp16" ? 2 : 3;
         p.CG_prec[k] = (int)value;
     }
+    else if (prec_suffix(n, "tuned_carveout") >= 0) {
+        if (value < -2 || value > 100) return DDP_ERR_INVALID_ARG;
+        p.carveout_prec[prec_suffix(n, "tuned_carveout")] = (int)value;
+    }
+    else return DDP_ERR_INVALID_ARG;
+    return DDP_OK;
+}
+
+int ddp_get_param(const ddp_ctx *ctx, const char *name, double *value) {
+    if (!ctx || !name || !value) return DDP_ERR_INVALID_ARG;
+    const EngineParams &p = ctx->prm;
+    const std::string n(name);
+    if (n == "max_outer") *value = p.max_outer;
+    else if (n == "max_inner") *value = p.max_inner;
+    else if (prec_suffix(n, "delta") >= 0) *value = p.floor_delta[prec_suffix(n, "delta")];
+    else if (n == "tile_sites") *value = HOP_TS;
+    else if (n == "tile_cols") *value = p.CG;
+    else if (n == "conditional") *value = p.use_conditional;
+    else if (n == "projector_tensor_cores") *value = p.proj_tc;
+    else if (n == "contraction_double_fp32") *value = p.contract_dd;
+    else if (n == "overlap_downloads") *value = p.overlap_downloads;
+    else if (n == "stencil_carveout") *value = p.carveout;
+    else if (prec_suffix(n, "tuned_cols") >= 0) *value = p.CG_prec[prec_suffix(n, "tuned_cols")];
+    else if (prec_suffix(n, "tuned_carveout") >= 0) *value = p.carveout_prec[prec_suffix(n, "tuned_carveout")];
     else return DDP_ERR_INVALID_ARG;
     return DDP_OK;
 }
@@ -1196,38 +1228,49 @@ int ddp_set_param(ddp_ctx *ctx, const char *name, double value) {
 long ddp_kernel_launches(const ddp_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 // Autotuner: time the three inner-loop stencil variants on the domain for every
-// admissible number of columns per block and keep, for this storage format, the
-// choice with the shortest stencil time of one BiCGStab iteration (two PLAIN
-// launches and one of each Schur variant).
+// admissible number of columns per block (the block shape: 32 sites x columns) and
+// every candidate shared-memory carveout of the stencils (the split of the unified
+// L1 / shared memory between the staged links of the resident blocks and the L1 that
+// serves the neighbour gathers: fewer columns per block means more resident blocks,
+// each staging its own links), and keep, for this storage format, the pair with the
+// shortest stencil time of one BiCGStab iteration (two PLAIN launches and one of each
+// Schur variant).
 int ddp_autotune(ddp_ctx *ctx, int domain_id, double kappa, int ncol, int precision, int iters, int *best_cols,
                  float *best_ms) {
     if (!ctx || ncol < 1 || precision < 0 || precision > 3 || iters < 1) return DDP_ERR_INVALID_ARG;
     const int cands[] = {12, 8, 6, 4, 3, 2, 1};
+    const int carves[] = {28, 50, 100};
     const int weight[3] = {2, 1, 1};
-    int saved = ctx->prm.CG, best = 0;
+    const int saved = ctx->prm.CG, saved_cv = ctx->prm.carveout_prec[precision];
+    int best = 0, best_cv = carves[0];
     float bms = 0;
-    ctx->prm.CG = 0;
-    for (int c : cands) {
-        if (c > ncol) continue;
-        ctx->prm.CG = c;
-        float tot = 0;
-        for (int k = DDP_HOP_PLAIN; k <= DDP_HOP_SCHUR_TS; k++) {
-            float ms = 0;
-            double by = 0;
-            int rc = ddp_time_hop(ctx, domain_id, kappa, ncol, precision, k, iters, &ms, &by);
-            if (rc) {
-                ctx->prm.CG = saved;
-                return rc;
+    for (int cv : carves) {
+        ctx->prm.carveout_prec[precision] = cv;
+        for (int c : cands) {
+            if (c > ncol) continue;
+            ctx->prm.CG = c;
+            float tot = 0;
+            for (int k = DDP_HOP_PLAIN; k <= DDP_HOP_SCHUR_TS; k++) {
+                float ms = 0;
+                double by = 0;
+                int rc = ddp_time_hop(ctx, domain_id, kappa, ncol, precision, k, iters, &ms, &by);
+                if (rc) {
+                    ctx->prm.CG = saved;
+                    ctx->prm.carveout_prec[precision] = saved_cv;
+                    return rc;
+                }
+                tot += weight[k] * ms;
             }
-            tot += weight[k] * ms;
-        }
-        if (!best || tot < bms) {
-            best = c;
-            bms = tot;
+            if (!best || tot < bms) {
+                best = c;
+                best_cv = cv;
+                bms = tot;
+            }
         }
     }
     ctx->prm.CG = saved;
     ctx->prm.CG_prec[precision] = best;
+    ctx->prm.carveout_prec[precision] = best_cv;
     if (best_cols) *best_cols = best;
     if (best_ms) *best_ms = bms;
     return DDP_OK;

@@ -84,12 +84,19 @@ struct EngineParams {
     // choice): 28 rounds up to the smallest carveout that holds three 19.6 KB blocks and
     // leaves the rest of the unified memory (about 192 KB) as L1 for the neighbour gathers
     int carveout = 28;
+    // the carveout ddp_autotune chose for a storage format (-2: none, use carveout)
+    int carveout_prec[4] = {-2, -2, -2, -2};
     int contract_dd = 1;        // nucleon contraction in double-FP32 arithmetic (0: FP64)
     int proj_tc = 1;            // projector-cut Gram blocks and colourless sums on the tensor cores (0: FP64 kernels)
     // ddp_propagator_series with host outputs: solve the smaller nested domains first and
     // download their results while the largest solves (0: one batched solve, then downloads)
     int overlap_downloads = 1;
 };
+
+// The stencil carveout of a storage format: the autotuner's choice, else the context's.
+inline int carveout_for(const EngineParams &p, int prec) {
+    return (prec >= 0 && prec < 4 && p.carveout_prec[prec] != -2) ? p.carveout_prec[prec] : p.carveout;
+}
 
 // A growable device arena owned by the context.
 struct Arena {

@@ -179,8 +179,8 @@ struct Engine {
 
     int build_loop_graph() {
         cudaStream_t st = ctx->stream;
-        DDP_CUDA(ctx, (set_hop_carveout<P, false>(ctx->prm.carveout)));
-        DDP_CUDA(ctx, (set_hop_carveout<P, true>(ctx->prm.carveout)));
+        DDP_CUDA(ctx, (set_hop_carveout<P, false>(carveout_for(ctx->prm, prec))));
+        DDP_CUDA(ctx, (set_hop_carveout<P, true>(carveout_for(ctx->prm, prec))));
         if (ctx->prm.use_conditional) {
             DDP_CUDA(ctx, cudaGraphCreate(&loop_graph, 0));
             cudaGraphConditionalHandle h;
@@ -645,7 +645,7 @@ int time_hop_impl(ddp_ctx *ctx, const Job &job, int prec, int kernel, int iters,
     h.v2 = none;
     h.rh = (kernel == DDP_HOP_SCHUR_RHAT) ? rhv : none;
     h.part = A;
-    DDP_CUDA(ctx, (set_hop_carveout<P, false>(ctx->prm.carveout)));
+    DDP_CUDA(ctx, (set_hop_carveout<P, false>(carveout_for(ctx->prm, prec))));
     auto launch = [&]() {
         if (kernel == DDP_HOP_PLAIN)
             launch_hop<P, EPI_PLAIN, DOT_NONE>(ctx, plan.nblocks, plan.TS * plan.CG, h);

@@ -470,14 +470,18 @@ def test_autotune_choice_keeps_results(ddp, ctx, field, tmp_path):
     cache = tmp_path / "tune.json"
     cols, ms = ddp.autotune_cached(ctx, did, n, 0.124, 12, ddp.DDP_PREC_MIXED_FP32, str(cache), iters=3)
     assert cols in (12, 8, 6, 4, 3, 2, 1) and ms > 0
+    carve = ddp.ddp_get_param(ctx, "tuned_carveout_fp32")
+    assert carve in (28, 50, 100) and ddp.ddp_get_param(ctx, "tuned_cols_fp32") == cols
+    ddp.ddp_set_param(ctx, "tuned_carveout_fp32", -2)
     again = ddp.autotune_cached(ctx, did, n, 0.124, 12, ddp.DDP_PREC_MIXED_FP32, str(cache))
-    assert again[0] == cols
+    assert again[0] == cols and ddp.ddp_get_param(ctx, "tuned_carveout_fp32") == carve
     S = torch.zeros((12, n, 4, 3), dtype=torch.complex128, device="cuda")
     rc, info = ddp.ddp_solve_propagator(ctx, did, 0.124, 0.0, (0, 0, 0, 0), 1e-10, 1, S)
     assert rc == ddp.DDP_OK
     ref, *_ = oracle.propagator(U, LAT, AP, o, e, 0.124, (0, 0, 0, 0), tol=1e-12)
     assert max(_col_errors(S.cpu().numpy(), ref)) < COL_TOL
     ddp.ddp_set_param(ctx, "tuned_cols_fp32", 0)
+    ddp.ddp_set_param(ctx, "tuned_carveout_fp32", -2)
 
 
 @pytest.mark.parametrize("box,src", [(BOXES[5], (7, 3, 1, 5)), (BOXES[6], (3, 2, 2, 4))])
