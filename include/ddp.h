@@ -310,7 +310,7 @@ int ddp_poll(ddp_ctx *ctx, uint64_t ticket, int *done, ddp_solve_info *info);
  * choice), "contraction_double_fp32" (1, the default: the nucleon contraction of
  * ddp_contract in double-FP32 arithmetic, relative error about 1e-13; 0: FP64),
  * "projector_tensor_cores" (1, the default: the Gram blocks and colourless
- * spinor sums of the projector cut, m <= 32, run as an emulated-FP64 product on the
+ * spinor sums of the projector cut, m <= 128, run as an emulated-FP64 product on the
  * tensor cores and the Cholesky-QR update A <- A R^-1 in double-FP32; 0: direct FP64
  * kernels), "overlap_downloads" (1, the default: ddp_propagator_series with host
  * outputs solves the smaller nested domains first and copies their results to the host
